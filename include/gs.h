@@ -1,0 +1,188 @@
+/*
+ * gs.h -- C ABI of the B300 depth/normal Gaussian-splat rasterizer (libgs.so).
+ *
+ * The library renders, for one or more views of one or more sets of 3D
+ * Gaussians, the colour map (alpha blending, Eq. 3 of RaDe-GS, arxiv
+ * 2406.01467), the alpha map, the rasterized planar depth map (Eq. 4 with the
+ * plane coefficients of Eq. 13-17 and the median rule of Sec. 1) and the normal
+ * map (Eq. 18-22), and the gradients of a loss on those maps with respect to
+ * the Gaussian parameters.
+ *
+ * Conventions
+ *   - camera frame: +x right, +y down, +z forward; viewmat is the row-major 4x4
+ *     world->camera matrix [R | t; 0 0 0 1] (W of Eq. 2 is R);
+ *   - pinhole u = fx x/z + cx, v = fy y/z + cy; pixel (i, j) is sampled at
+ *     (i + 0.5, j + 0.5);
+ *   - quaternions (w, x, y, z), normalised inside; scales > 0 and opacities in
+ *     (0, 1] are already activated (Eq. 1: Sigma = R S S^T R^T);
+ *   - SH coefficients [n][(deg+1)^2][3], real basis with Condon-Shortley phase,
+ *     colour = max(SH(dir) + 0.5, 0), dir = normalize(mean - camera centre);
+ *   - output maps are FP32, planar: colour and normal [3][H][W], alpha and depth
+ *     [H][W]; the views' maps are concatenated in view order.
+ *
+ * Ownership: every pointer is caller-owned device memory except the gs_* structs
+ * themselves, which are read on the host during the call and may be freed
+ * afterwards.  The library allocates nothing, keeps no state between calls
+ * apart from a thread-local error string, and never synchronises the stream:
+ * a gs_preprocess / gs_bin / gs_render_fwd / gs_render_bwd sequence can be
+ * captured in a CUDA graph.  Device-side problems (pair capacity exceeded,
+ * non-finite inputs) set a sticky word inside the workspace that gs_check reads.
+ *
+ * Errors: argument errors are detected on the host and returned at once
+ * (GS_ERR_INVALID_ARG, nothing is enqueued); a failed launch returns
+ * GS_ERR_CUDA.  gs_last_error_string() describes the last non-OK status of the
+ * calling thread.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is out of range */
+  GS_ERR_CAPACITY = 2,    /* more (tile, Gaussian) pairs than pair_capacity */
+  GS_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+  GS_ERR_TIMEOUT = 4,     /* reserved: a bounded device wait ran out */
+  GS_ERR_NUMERIC = 5      /* non-finite inputs; those Gaussians were culled */
+} gs_status;
+
+typedef enum { GS_F32 = 0, GS_BF16 = 1 } gs_dtype;
+
+enum { GS_MAX_VIEWS = 64, GS_MAX_SCENES = 16 };
+
+/* One set of Gaussians (Sec. 3.1).  All arrays are device pointers of the
+ * element type `dtype`, contiguous, row-major. */
+typedef struct {
+  const void* means;     /* [n][3] world-space centres x_c */
+  const void* scales;    /* [n][3] activated scales (diagonal of S) */
+  const void* quats;     /* [n][4] rotation quaternions (w, x, y, z) */
+  const void* opacities; /* [n]    activated opacities */
+  const void* sh;        /* [n][(sh_degree+1)^2][3] SH coefficients */
+  int64_t n;             /* number of Gaussians, >= 0 */
+  int32_t sh_degree;     /* 0..3 */
+  int32_t dtype;         /* gs_dtype of every array above */
+} gs_scene;
+
+/* One camera (Sec. 3.1: W is the world->camera rotation). */
+typedef struct {
+  float viewmat[16];  /* row-major world->camera */
+  float fx, fy, cx, cy;
+  int32_t width, height; /* 1..16384 */
+  float near_plane;      /* Gaussians with camera z <= near_plane are culled */
+  int32_t scene;         /* index of the gs_scene this view renders */
+} gs_view;
+
+/* Render parameters; the paper keeps the 3D GS defaults (Sec. 4.1.1). */
+typedef struct {
+  int32_t tile_w, tile_h; /* tile size; tile_w * tile_h must be 64, 128 or 256 */
+  float lowpass;          /* px^2 added to the 2x2 screen covariance, >= 0 */
+  float alpha_min;        /* in (0, 1): splats below it are skipped at a pixel */
+  float alpha_max;        /* in [alpha_min, 1): alpha clamp */
+  float T_min;            /* in [0, 1): stop before T would fall below it */
+  float median_T;         /* in (0, 1): median depth threshold on T */
+  float clamp_margin;     /* x/z, y/z inside J clamped to the image widened by this */
+} gs_params;
+
+/* Everything a call needs to know about one frame (a batch of views). */
+typedef struct {
+  const gs_scene* scenes; /* host array [n_scenes] */
+  int32_t n_scenes;       /* 1..GS_MAX_SCENES */
+  const gs_view* views;   /* host array [n_views] */
+  int32_t n_views;        /* 1..GS_MAX_VIEWS */
+  gs_params params;
+  int64_t pair_capacity;  /* maximum (tile, Gaussian) pairs, >= 1 */
+  void* workspace;        /* device, 256-byte aligned, gs_workspace_size() bytes */
+  size_t workspace_bytes;
+} gs_frame;
+
+/* Output maps (device, FP32), all views concatenated. */
+typedef struct {
+  float* color;  /* [sum_v 3 H_v W_v] */
+  float* alpha;  /* [sum_v H_v W_v]   1 - final transmittance */
+  float* depth;  /* [sum_v H_v W_v]   median planar depth, 0 where nothing blends */
+  float* normal; /* [sum_v 3 H_v W_v] blended camera-space unit normals */
+} gs_maps;
+
+/* Upstream gradients dL/d(maps), same layouts as gs_maps; any may be NULL (zero). */
+typedef struct {
+  const float* dcolor;
+  const float* dalpha;
+  const float* ddepth;
+  const float* dnormal;
+} gs_map_grads;
+
+/* Parameter gradients of one scene (device, FP32, same shapes as gs_scene's
+ * arrays).  They are overwritten, not accumulated.  Any pointer may be NULL. */
+typedef struct {
+  float* dmeans;
+  float* dscales;
+  float* dquats;
+  float* dopacities;
+  float* dsh;
+} gs_scene_grads;
+
+/* Counters read back by gs_check. */
+typedef struct {
+  int64_t n_entries;    /* (view, Gaussian) entries processed */
+  int64_t n_visible;    /* entries that touch at least one pixel */
+  int64_t n_pairs;      /* (tile, Gaussian) pairs needed */
+  int64_t n_nonfinite;  /* entries culled for non-finite inputs */
+  int32_t status;       /* sticky gs_status of the device work */
+} gs_stats;
+
+/* Bytes of workspace the frame needs (its workspace fields are ignored).
+ * Returns 0 and sets the error string on invalid arguments. */
+size_t gs_workspace_size(const gs_frame* frame);
+
+/* Per-Gaussian stage (Eq. 1-2, 8-22): projection, EWA covariance and conic,
+ * SH colour, depth-plane coefficients p (Eq. 15-17) and normal (Eq. 22) for
+ * every (view, Gaussian) entry; culling; pixel and tile rectangles; depth keys.
+ * Resets the workspace's counters and sticky status.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream). */
+gs_status gs_preprocess(const gs_frame* frame, void* stream);
+
+/* Binning (inherited from 3D GS, Sec. 4.1.1): orders visible entries by depth
+ * (own LSD radix sort), emits one pair per overlapped tile, sorts the pairs by
+ * tile (stable, so each tile's list stays in depth order, ties by Gaussian
+ * index) and finds each tile's [start, end).  Sets GS_ERR_CAPACITY on the
+ * device if the pairs exceed pair_capacity; later stages then do nothing. */
+gs_status gs_bin(const gs_frame* frame, void* stream);
+
+/* Front-to-back compositing (Eq. 3, Eq. 4, Sec. 1, Eq. 22) of every view into
+ * `maps`; stores the per-pixel state the backward pass replays. */
+gs_status gs_render_fwd(const gs_frame* frame, const gs_maps* maps, void* stream);
+
+/* Backward of gs_render_fwd and of gs_preprocess: replays each pixel back to
+ * front and writes dL/d(means, scales, quats, opacities, sh) for every scene
+ * (`grads` is a host array [n_scenes]). */
+gs_status gs_render_bwd(const gs_frame* frame, const gs_map_grads* dmaps,
+                        const gs_scene_grads* grads, void* stream);
+
+/* Intermediate results for tests and tools, copied to caller device buffers on
+ * `stream`; any pointer may be NULL.  rec: [n_entries][16] FP32 per-entry
+ * records (u, v, conic a b c, opacity, z, p0 | p1, n0 n1 n2, r g b, spare);
+ * rect: [n_entries][4] int32 pixel rectangle (i0, i1, j0, j1), (0,-1,0,-1)
+ * when culled; pair_tile/pair_entry: [pair_capacity] int32 sorted pairs;
+ * ranges: [total tiles][2] int32.  grad2d: [n_entries][16] FP32 dL/d(record),
+ * valid after gs_render_bwd. */
+gs_status gs_debug_copy(const gs_frame* frame, float* rec, int32_t* rect,
+                        int32_t* pair_tile, int32_t* pair_entry, int32_t* ranges,
+                        float* grad2d, void* stream);
+
+/* Synchronises `stream`, then reads the counters and sticky status. */
+gs_status gs_check(const gs_frame* frame, gs_stats* out, void* stream);
+
+/* Human-readable description of the calling thread's last error. */
+const char* gs_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H_ */

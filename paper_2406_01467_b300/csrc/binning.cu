@@ -1,0 +1,416 @@
+// Binning of projected Gaussians into screen tiles (the 3D GS tile scheme the
+// paper builds on, Sec. 4.1.1), with an own stable LSD radix sort.
+//
+// Plan (all counts stay on the device, nothing is read back):
+//   1. compact the visible entries -> (depth key, entry) lists;
+//   2. sort them by depth key (4 passes of 8 bits; stable, so equal depths keep
+//      entry order);
+//   3. exclusive scan of tiles_touched in depth order -> pair offsets and the
+//      pair count (checked against the capacity);
+//   4. emit one (tile, entry) pair per overlapped tile, in depth order;
+//   5. stable sort of the pairs by tile id (ceil(log2 T)/8 passes): every tile's
+//      list is then in (depth, entry) order, the same order as a full sort on
+//      (tile, depth bits, entry) keys;
+//   6. [start, end) of each tile.
+// Each radix pass is reduce-then-scan (histogram, per-digit scan, stable
+// scatter); no kernel waits on another block.
+#include <algorithm>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+__device__ inline int64_t clamp_count(const unsigned long long* p, int64_t cap) {
+  unsigned long long c = *p;
+  return (int64_t)(c < (unsigned long long)cap ? c : (unsigned long long)cap);
+}
+
+__device__ inline unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Block-wide exclusive scan of one uint32 per thread (256 threads).
+__device__ inline uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+    uint32_t s = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(FULL, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < (int)(blockDim.x >> 5)) s_warp[lane] = s - t;
+    if (lane == 31) s_warp[32] = s;
+  }
+  __syncthreads();
+  uint32_t r = x - v + s_warp[w];
+  if (total) *total = s_warp[32];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Generic per-block partial sums and the scan of those partials
+// ---------------------------------------------------------------------------
+// mode 0: count entries with a valid depth key (items = entries)
+// mode 1: sum tiles_touched over depth-sorted entries (items = visible entries)
+template <int MODE>
+__global__ void __launch_bounds__(kSortThreads)
+k_block_sums(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
+             const unsigned long long* count_ptr, int64_t n_fixed, uint32_t* blk) {
+  __shared__ uint32_t s_warp[33];
+  const int64_t n = count_ptr ? clamp_count(count_ptr, n_fixed) : n_fixed;
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  uint32_t sum = 0;
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = base + r * kSortThreads + threadIdx.x;
+    if (i < n) {
+      if (MODE == 0) sum += a[i] != kInvalidKey ? 1u : 0u;
+      else sum += a[b[i]];
+    }
+  }
+  uint32_t tot;
+  block_exclusive_scan(sum, s_warp, &tot);
+  if (threadIdx.x == 0) blk[blockIdx.x] = tot;
+}
+
+// One block: exclusive scan of nb partials in place; the grand total goes to
+// *total_out.  If cap > 0 and the total exceeds it, the capacity error is set.
+__global__ void __launch_bounds__(1024)
+k_scan_partials(uint32_t* blk, int nb, unsigned long long* total_out, int64_t cap, Header* hdr) {
+  __shared__ uint32_t s_warp[33];
+  __shared__ unsigned long long s_run;
+  if (threadIdx.x == 0) s_run = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < nb; base += 1024) {
+    int i = base + threadIdx.x;
+    uint32_t v = i < nb ? blk[i] : 0u;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t t = s_warp[lane];
+      uint32_t s = t;
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, s, o);
+        if (lane >= o) s += y;
+      }
+      s_warp[lane] = s - t;
+      if (lane == 31) s_warp[32] = s;
+    }
+    __syncthreads();
+    unsigned long long run = s_run;
+    if (i < nb) blk[i] = (uint32_t)(run + (x - v) + s_warp[w]);
+    __syncthreads();
+    if (threadIdx.x == 0) s_run = run + s_warp[32];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *total_out = s_run;
+    if (cap > 0 && s_run > (unsigned long long)cap) set_status(hdr, GS_ERR_CAPACITY);
+  }
+}
+
+// In-block ordered scan helper: each warp owns 512 consecutive items
+// (16 rounds of 32), so item order = (warp, round, lane).
+struct WarpItems {
+  static __device__ inline int64_t index(int64_t base, int r) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    return base + (int64_t)w * (32 * kSortItems) + r * 32 + lane;
+  }
+};
+
+// Compaction of visible entries: (key, entry) at their rank among visible ones.
+__global__ void __launch_bounds__(kSortThreads)
+k_compact(const uint32_t* __restrict__ key, int64_t E, const uint32_t* __restrict__ blk,
+          uint32_t* __restrict__ okey, uint32_t* __restrict__ oval) {
+  __shared__ uint32_t s_wtot[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  uint32_t k[kSortItems];
+  uint32_t wsum = 0;
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = WarpItems::index(base, r);
+    k[r] = i < E ? key[i] : kInvalidKey;
+    wsum += __popc(__ballot_sync(FULL, k[r] != kInvalidKey));
+  }
+  if (lane == 0) s_wtot[w] = wsum;
+  __syncthreads();
+  uint32_t off = blk[blockIdx.x];
+  for (int i = 0; i < w; ++i) off += s_wtot[i];
+  for (int r = 0; r < kSortItems; ++r) {
+    const bool v = k[r] != kInvalidKey;
+    const unsigned bal = __ballot_sync(FULL, v);
+    if (v) {
+      uint32_t pos = off + __popc(bal & lanemask_lt());
+      okey[pos] = k[r];
+      oval[pos] = (uint32_t)WarpItems::index(base, r);
+    }
+    off += __popc(bal);
+  }
+}
+
+// Emission of (tile, entry) pairs in depth order.
+__global__ void __launch_bounds__(kSortThreads)
+k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
+       const unsigned long long* n_vis_ptr, int64_t E, const uint32_t* __restrict__ touched,
+       const short4* __restrict__ rect, const uint32_t* __restrict__ blk, int64_t cap,
+       uint32_t* __restrict__ ptile, uint32_t* __restrict__ pval) {
+  __shared__ uint32_t s_wtot[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t n = clamp_count(n_vis_ptr, E);
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (base >= n) return;
+  uint32_t ent[kSortItems], cnt[kSortItems];
+  uint32_t wsum = 0;
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = WarpItems::index(base, r);
+    ent[r] = i < n ? sval[i] : 0u;
+    cnt[r] = i < n ? touched[ent[r]] : 0u;
+    uint32_t x = cnt[r];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    wsum += x;
+  }
+  if (lane == 0) s_wtot[w] = wsum;
+  __syncthreads();
+  uint64_t off = blk[blockIdx.x];
+  for (int i = 0; i < w; ++i) off += s_wtot[i];
+  const int nv = fd->n_views;
+  const int sx = fd->tile_shift_x, sy = fd->tile_shift_y;
+  for (int r = 0; r < kSortItems; ++r) {
+    uint32_t x = cnt[r];
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    uint64_t my = off + x - cnt[r];
+    off += __shfl_sync(FULL, x, 31);
+    if (cnt[r] == 0) continue;
+    const uint32_t e = ent[r];
+    const int vi = find_view(fd->entry_off, nv, (int64_t)e);
+    const int tx_n = fd->views[vi].tiles_x;
+    const int toff = fd->tile_off[vi];
+    const short4 rc = rect[e];
+    const int tx0 = rc.x >> sx, tx1 = rc.y >> sx, ty0 = rc.z >> sy, ty1 = rc.w >> sy;
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) {
+        if (my < (uint64_t)cap) {
+          ptile[my] = (uint32_t)(toff + ty * tx_n + tx);
+          pval[my] = e;
+        }
+        ++my;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Radix sort pass: histogram, per-digit scan over blocks, stable scatter
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_hist(const uint32_t* __restrict__ kin, const unsigned long long* count_ptr, int64_t cap,
+             int shift, uint32_t* __restrict__ hist, int nb) {
+  __shared__ uint32_t s_h[8][kRadix];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&s_h[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t n = clamp_count(count_ptr, cap);
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (base < n) {
+    for (int r = 0; r < kSortItems; ++r) {
+      int64_t i = WarpItems::index(base, r);
+      int d = i < n ? (int)((kin[i] >> shift) & (kRadix - 1)) : kRadix;
+      unsigned peers = __match_any_sync(FULL, d);
+      if (d < kRadix && (peers & lanemask_lt()) == 0) s_h[w][d] += __popc(peers);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  const int d = threadIdx.x;
+  uint32_t s = 0;
+  for (int i = 0; i < 8; ++i) s += s_h[i][d];
+  hist[(int64_t)d * nb + blockIdx.x] = s;
+  (void)lane;
+}
+
+// Block d scans hist[d][0..nb) (exclusive, in place) and writes the digit total.
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_scan(uint32_t* __restrict__ hist, int nb, uint32_t* __restrict__ tot) {
+  __shared__ uint32_t s_warp[33];
+  uint32_t* h = hist + (int64_t)blockIdx.x * nb;
+  const int per = (nb + kSortThreads - 1) / kSortThreads;
+  const int b0 = threadIdx.x * per;
+  uint32_t sum = 0;
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < nb) sum += h[b0 + i];
+  uint32_t total;
+  uint32_t off = block_exclusive_scan(sum, s_warp, &total);
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < nb) {
+      uint32_t v = h[b0 + i];
+      h[b0 + i] = off;
+      off += v;
+    }
+  if (threadIdx.x == 0) tot[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                const unsigned long long* count_ptr, int64_t cap, int shift,
+                const uint32_t* __restrict__ hist, const uint32_t* __restrict__ tot, int nb) {
+  __shared__ uint32_t s_wcnt[kRadix][8];
+  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_dstart[kRadix];
+  __shared__ uint32_t s_gbase[kRadix];
+  __shared__ uint32_t s_warp[33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t n = clamp_count(count_ptr, cap);
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (base >= n) return;
+  for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
+  // global start of each digit for this block
+  {
+    const int d = threadIdx.x;
+    uint32_t t = tot[d];
+    uint32_t dbase = block_exclusive_scan(t, s_warp, nullptr);
+    s_gbase[d] = dbase + hist[(int64_t)d * nb + blockIdx.x];
+  }
+  __syncthreads();
+  uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
+  const unsigned lt = lanemask_lt();
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = WarpItems::index(base, r);
+    const bool ok = i < n;
+    k[r] = ok ? kin[i] : 0u;
+    v[r] = ok ? vin[i] : 0u;
+    int d = ok ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
+    unsigned peers = __match_any_sync(FULL, d);
+    uint32_t old = d < kRadix ? s_wcnt[d][w] : 0u;
+    rank[r] = old + __popc(peers & lt);
+    __syncwarp();
+    if (d < kRadix && (peers & lt) == 0) s_wcnt[d][w] = old + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // block-local exclusive scan over (digit, warp) in digit-major order
+  {
+    const int d = threadIdx.x;
+    uint32_t c[8], s = 0;
+    for (int i = 0; i < 8; ++i) { c[i] = s_wcnt[d][i]; s += c[i]; }
+    uint32_t start = block_exclusive_scan(s, s_warp, nullptr);
+    s_dstart[d] = start;
+    uint32_t run = start;
+    for (int i = 0; i < 8; ++i) { s_wcnt[d][i] = run; run += c[i]; }
+  }
+  __syncthreads();
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = WarpItems::index(base, r);
+    if (i < n) {
+      int d = (int)((k[r] >> shift) & (kRadix - 1));
+      uint32_t pos = s_wcnt[d][w] + rank[r];
+      s_keys[pos] = k[r];
+      s_vals[pos] = v[r];
+    }
+  }
+  __syncthreads();
+  const int nloc = (int)min((int64_t)kSortTile, n - base);
+  for (int i = threadIdx.x; i < nloc; i += kSortThreads) {
+    uint32_t kk = s_keys[i];
+    int d = (int)((kk >> shift) & (kRadix - 1));
+    uint32_t dst = s_gbase[d] + (uint32_t)i - s_dstart[d];
+    kout[dst] = kk;
+    vout[dst] = s_vals[i];
+  }
+  (void)lane;
+}
+
+__global__ void __launch_bounds__(256)
+k_ranges(const uint32_t* __restrict__ ptile, const unsigned long long* n_pairs_ptr, int64_t cap,
+         int2* __restrict__ ranges) {
+  const int64_t P = clamp_count(n_pairs_ptr, cap);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t t = ptile[i];
+    if (i == 0 || ptile[i - 1] != t) ranges[t].x = (int)i;
+    if (i == P - 1 || ptile[i + 1] != t) ranges[t].y = (int)(i + 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+static cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                              const unsigned long long* count, int64_t cap, int nb, int bits,
+                              uint32_t* hist, uint32_t* tot, cudaStream_t s) {
+  uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+  for (int shift = 0; shift < bits; shift += kRadixBits) {
+    k_radix_hist<<<nb, kSortThreads, 0, s>>>(ki, count, cap, shift, hist, nb);
+    k_radix_scan<<<kRadix, kSortThreads, 0, s>>>(hist, nb, tot);
+    k_radix_scatter<<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, cap, shift, hist, tot, nb);
+    uint32_t* t;
+    t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+  }
+  return cudaGetLastError();
+}
+
+int tile_sort_bits(int64_t n_tiles) {
+  int bits = 0;
+  while ((int64_t(1) << bits) < n_tiles) ++bits;
+  return bits < 1 ? 1 : bits;
+}
+
+cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream_t s) {
+  const FrameDev* fd = at<FrameDev>(ws, L.frame);
+  Header* hdr = at<Header>(ws, L.hdr);
+  uint32_t* key = at<uint32_t>(ws, L.key);
+  uint32_t* touched = at<uint32_t>(ws, L.touched);
+  uint32_t* blk = at<uint32_t>(ws, L.blk);
+  uint32_t* hist = at<uint32_t>(ws, L.hist);
+  uint32_t* tot = at<uint32_t>(ws, L.htot);
+  uint32_t *vk0 = at<uint32_t>(ws, L.vkey[0]), *vk1 = at<uint32_t>(ws, L.vkey[1]);
+  uint32_t *vv0 = at<uint32_t>(ws, L.vval[0]), *vv1 = at<uint32_t>(ws, L.vval[1]);
+  uint32_t *pt0 = at<uint32_t>(ws, L.ptile[0]), *pt1 = at<uint32_t>(ws, L.ptile[1]);
+  uint32_t *pv0 = at<uint32_t>(ws, L.pval[0]), *pv1 = at<uint32_t>(ws, L.pval[1]);
+  (void)hf;
+  // 1. compaction
+  k_block_sums<0><<<L.nb_E, kSortThreads, 0, s>>>(key, nullptr, nullptr, L.E, blk);
+  k_scan_partials<<<1, 1024, 0, s>>>(blk, L.nb_E, &hdr->n_vis, 0, hdr);
+  k_compact<<<L.nb_E, kSortThreads, 0, s>>>(key, L.E, blk, vk0, vv0);
+  // 2. depth sort: 31 bits (z > 0, so the sign bit is clear)
+  cudaError_t err = radix_sort(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, hist, tot, s);
+  if (err != cudaSuccess) return err;
+  // 3. pair offsets
+  k_block_sums<1><<<L.nb_E, kSortThreads, 0, s>>>(touched, vv0, &hdr->n_vis, L.E, blk);
+  k_scan_partials<<<1, 1024, 0, s>>>(blk, L.nb_E, &hdr->n_pairs, L.Pcap, hdr);
+  // 4. emission
+  k_emit<<<L.nb_E, kSortThreads, 0, s>>>(fd, vv0, &hdr->n_vis, L.E, touched,
+                                         at<short4>(ws, L.rect), blk, L.Pcap, pt0, pv0);
+  // 5. tile sort
+  const int bits = tile_sort_bits(L.T);
+  err = radix_sort(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, hist, tot, s);
+  if (err != cudaSuccess) return err;
+  uint32_t* ptile = at<uint32_t>(ws, L.ptile_final);
+  // 6. ranges
+  cudaMemsetAsync(at<int2>(ws, L.ranges), 0, sizeof(int2) * (size_t)L.T, s);
+  int g = (int)std::min<int64_t>((L.Pcap + 255) / 256, 148 * 32);
+  k_ranges<<<g, 256, 0, s>>>(ptile, &hdr->n_pairs, L.Pcap, at<int2>(ws, L.ranges));
+  return cudaGetLastError();
+}
+
+}  // namespace gs

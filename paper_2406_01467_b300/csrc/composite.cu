@@ -1,0 +1,311 @@
+// Per-tile compositing: front-to-back forward and back-to-front backward.
+//
+// Forward, per pixel (one thread), over its tile's depth-ordered list, staged
+// through shared memory one batch of records at a time:
+//   Delta = (u_c - u, v_c - v); sigma = 1/2 Delta^T conic Delta;
+//   alpha = min(alpha_max, o exp(-sigma)), skipped below alpha_min;
+//   stop before T (1 - alpha) < T_min;  w = alpha T;
+//   colour += w rgb (Eq. 3); normal += w n (Eq. 22);
+//   depth = z_c + p Delta (Eq. 4) of the first splat with T' <= median_T
+//   (the median depth of Sec. 1), else of the last contributor;
+//   alpha map = 1 - T_final.
+// The block leaves the loop as soon as every pixel of the tile is done.
+//
+// Backward replays each pixel from its last contributor toward the front,
+// recovering T by division (alpha <= alpha_max < 1) and the colour / normal
+// "behind" sums recursively; nothing per (pixel, splat) is stored.  Each warp
+// reduces the 15 per-splat gradients of its 32 pixels with a transposed
+// reduce-scatter (16 shuffles instead of 75) and issues one vector of atomics.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+struct TileCtx {
+  int view, px, py, W, H;
+  bool inside;
+  int64_t pix;        // global pixel index (concatenated views)
+  int64_t pix_local;  // index inside the view
+  int64_t pix_base;   // first pixel of the view
+};
+
+__device__ inline TileCtx tile_ctx(const FrameDev* fd, int tile) {
+  TileCtx c;
+  c.view = find_view_tile(fd->tile_off, fd->n_views, tile);
+  const ViewDev& V = fd->views[c.view];
+  const int local = tile - fd->tile_off[c.view];
+  const int tx = local % V.tiles_x, ty = local / V.tiles_x;
+  c.px = tx * fd->tile_w + (int)(threadIdx.x % fd->tile_w);
+  c.py = ty * fd->tile_h + (int)(threadIdx.x / fd->tile_w);
+  c.W = V.width;
+  c.H = V.height;
+  c.inside = c.px < c.W && c.py < c.H;
+  c.pix_base = fd->pix_off[c.view];
+  c.pix_local = (int64_t)c.py * c.W + c.px;
+  c.pix = c.pix_base + c.pix_local;
+  return c;
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_maps maps) {
+  __shared__ float4 s_a[BLOCK], s_b[BLOCK], s_c[BLOCK], s_d[BLOCK];
+  const Header* hdr = at<Header>(ws, L.hdr);
+  if (hdr->status == GS_ERR_CAPACITY) return;
+  const int tile = blockIdx.x;
+  const TileCtx c = tile_ctx(fd, tile);
+  const int2 range = at<int2>(ws, L.ranges)[tile];
+  const uint32_t* pval = at<uint32_t>(ws, L.pval_final);
+  const float4* rec = at<float4>(ws, L.rec);
+  const float amin = fd->alpha_min, amax = fd->alpha_max, tmin = fd->T_min, tmed = fd->median_T;
+  const float fpx = c.px + 0.5f, fpy = c.py + 0.5f;
+
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, depth = 0.f;
+  int last = -1, med = -1;
+  bool done = !c.inside;
+  for (int b0 = range.x; b0 < range.y; b0 += BLOCK) {
+    if (__syncthreads_count(done) == BLOCK) break;
+    const int i = b0 + threadIdx.x;
+    if (i < range.y) {
+      const float4* r = rec + 4 * (int64_t)pval[i];
+      s_a[threadIdx.x] = r[0];
+      s_b[threadIdx.x] = r[1];
+      s_c[threadIdx.x] = r[2];
+      s_d[threadIdx.x] = r[3];
+    }
+    __syncthreads();
+    const int nb = min(BLOCK, range.y - b0);
+    for (int j = 0; !done && j < nb; ++j) {
+      const float4 a = s_a[j], b = s_b[j];
+      const float dx = a.x - fpx, dy = a.y - fpy;
+      const float sig = 0.5f * (a.z * dx * dx + b.x * dy * dy) + a.w * dx * dy;
+      const float al = fminf(amax, b.y * __expf(-sig));
+      if (sig < 0.f || al < amin) continue;
+      const float Tn = T * (1.f - al);
+      if (Tn < tmin) { done = true; break; }
+      const float w = al * T;
+      const float4 cc = s_c[j], d = s_d[j];
+      C0 += w * d.x; C1 += w * d.y; C2 += w * d.z;
+      N0 += w * cc.y; N1 += w * cc.z; N2 += w * cc.w;
+      if (med < 0 && Tn <= tmed) {
+        med = b0 + j;
+        depth = b.z + b.w * dx + cc.x * dy;
+      }
+      last = b0 + j;
+      T = Tn;
+    }
+  }
+  if (!c.inside) return;
+  if (med < 0 && last >= 0) {   // median never reached: depth of the last contributor
+    med = last;
+    const float4* r = rec + 4 * (int64_t)pval[last];
+    const float4 a = r[0], b = r[1], cc = r[2];
+    depth = b.z + b.w * (a.x - fpx) + cc.x * (a.y - fpy);
+  }
+  const int64_t HW = (int64_t)c.W * c.H;
+  const int64_t p = c.pix_local;
+  if (maps.color) {
+    float* col = maps.color + 3 * c.pix_base;
+    col[p] = C0; col[HW + p] = C1; col[2 * HW + p] = C2;
+  }
+  if (maps.normal) {
+    float* nrm = maps.normal + 3 * c.pix_base;
+    nrm[p] = N0; nrm[HW + p] = N1; nrm[2 * HW + p] = N2;
+  }
+  if (maps.alpha) maps.alpha[c.pix] = 1.f - T;
+  if (maps.depth) maps.depth[c.pix] = depth;
+  at<float>(ws, L.px_T)[c.pix] = T;
+  at<int>(ws, L.px_last)[c.pix] = last;
+  at<int>(ws, L.px_med)[c.pix] = med;
+}
+
+// Transposed warp reduce-scatter of 16 values: afterwards lane l holds the
+// warp-wide sum of slot (l >> 1) (lanes l and l^1 hold the same value).
+__device__ inline float warp_reduce_scatter16(float (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool hi = lane & 16;
+    const float send = hi ? v[i] : v[i + 8];
+    const float keep = hi ? v[i + 8] : v[i];
+    v[i] = keep + __shfl_xor_sync(kFull, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool hi = lane & 8;
+    const float send = hi ? v[i] : v[i + 4];
+    const float keep = hi ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(kFull, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool hi = lane & 4;
+    const float send = hi ? v[i] : v[i + 2];
+    const float keep = hi ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(kFull, send, 4);
+  }
+  {
+    const bool hi = lane & 2;
+    const float send = hi ? v[0] : v[1];
+    const float keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(kFull, send, 2);
+  }
+  return v[0] + __shfl_xor_sync(kFull, v[0], 1);
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_map_grads g) {
+  __shared__ float4 s_a[BLOCK], s_b[BLOCK], s_c[BLOCK], s_d[BLOCK];
+  __shared__ uint32_t s_e[BLOCK];
+  __shared__ int s_max;
+  const Header* hdr = at<Header>(ws, L.hdr);
+  if (hdr->status == GS_ERR_CAPACITY) return;
+  const int tile = blockIdx.x;
+  const TileCtx c = tile_ctx(fd, tile);
+  const int2 range = at<int2>(ws, L.ranges)[tile];
+  const uint32_t* pval = at<uint32_t>(ws, L.pval_final);
+  const float4* rec = at<float4>(ws, L.rec);
+  float* grad = at<float>(ws, L.grad2d);
+  const float amin = fd->alpha_min, amax = fd->alpha_max;
+  const float fpx = c.px + 0.5f, fpy = c.py + 0.5f;
+  const int lane = threadIdx.x & 31;
+
+  float Tf = 1.f;
+  int last = -1, med = -1;
+  float dC[3] = {0.f, 0.f, 0.f}, dN[3] = {0.f, 0.f, 0.f}, dA = 0.f, dD = 0.f;
+  if (c.inside) {
+    Tf = at<float>(ws, L.px_T)[c.pix];
+    last = at<int>(ws, L.px_last)[c.pix];
+    med = at<int>(ws, L.px_med)[c.pix];
+    const int64_t HW = (int64_t)c.W * c.H, p = c.pix_local;
+    if (g.dcolor) {
+      const float* d = g.dcolor + 3 * c.pix_base;
+      dC[0] = d[p]; dC[1] = d[HW + p]; dC[2] = d[2 * HW + p];
+    }
+    if (g.dnormal) {
+      const float* d = g.dnormal + 3 * c.pix_base;
+      dN[0] = d[p]; dN[1] = d[HW + p]; dN[2] = d[2 * HW + p];
+    }
+    if (g.dalpha) dA = g.dalpha[c.pix];
+    if (g.ddepth) dD = g.ddepth[c.pix];
+  }
+  if (threadIdx.x == 0) s_max = -1;
+  __syncthreads();
+  if (last >= 0) atomicMax(&s_max, last);
+  __syncthreads();
+  const int end = s_max + 1;
+
+  float T = Tf;
+  float Sc[3] = {0.f, 0.f, 0.f}, Sn[3] = {0.f, 0.f, 0.f};
+  for (int b1 = end; b1 > range.x; b1 -= BLOCK) {
+    const int b0 = max(range.x, b1 - BLOCK);
+    __syncthreads();
+    const int i = b1 - 1 - (int)threadIdx.x;
+    if (i >= b0) {
+      const uint32_t e = pval[i];
+      const float4* r = rec + 4 * (int64_t)e;
+      s_e[threadIdx.x] = e;
+      s_a[threadIdx.x] = r[0];
+      s_b[threadIdx.x] = r[1];
+      s_c[threadIdx.x] = r[2];
+      s_d[threadIdx.x] = r[3];
+    }
+    __syncthreads();
+    const int n = b1 - b0;
+    for (int j = 0; j < n; ++j) {
+      const int idx = b1 - 1 - j;
+      float gr[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) gr[k] = 0.f;
+      bool contrib = false;
+      if (idx <= last) {
+        const float4 a = s_a[j], b = s_b[j];
+        const float dx = a.x - fpx, dy = a.y - fpy;
+        const float sig = 0.5f * (a.z * dx * dx + b.x * dy * dy) + a.w * dx * dy;
+        const float G = __expf(-sig);
+        const float raw = b.y * G;
+        const float al = fminf(amax, raw);
+        if (sig >= 0.f && al >= amin) {
+          contrib = true;
+          const float4 cc = s_c[j], d = s_d[j];
+          const float ia = 1.f / (1.f - al);
+          T *= ia;                         // transmittance in front of this splat
+          const float w = al * T;
+          gr[R_R] = w * dC[0]; gr[R_G] = w * dC[1]; gr[R_B] = w * dC[2];
+          gr[R_N0] = w * dN[0]; gr[R_N1] = w * dN[1]; gr[R_N2] = w * dN[2];
+          float dal = T * ((d.x - Sc[0]) * dC[0] + (d.y - Sc[1]) * dC[1] + (d.z - Sc[2]) * dC[2] +
+                           (cc.y - Sn[0]) * dN[0] + (cc.z - Sn[1]) * dN[1] + (cc.w - Sn[2]) * dN[2]) +
+                      dA * Tf * ia;
+          Sc[0] = al * d.x + (1.f - al) * Sc[0];
+          Sc[1] = al * d.y + (1.f - al) * Sc[1];
+          Sc[2] = al * d.z + (1.f - al) * Sc[2];
+          Sn[0] = al * cc.y + (1.f - al) * Sn[0];
+          Sn[1] = al * cc.z + (1.f - al) * Sn[1];
+          Sn[2] = al * cc.w + (1.f - al) * Sn[2];
+          float gu = 0.f, gv = 0.f;
+          if (idx == med) {            // d = z_c + p . Delta (Eq. 4)
+            gr[R_Z] = dD;
+            gr[R_P0] = dD * dx;
+            gr[R_P1] = dD * dy;
+            gu += dD * b.w;
+            gv += dD * cc.x;
+          }
+          if (raw <= amax) {
+            gr[R_O] = dal * G;
+            const float gs = -dal * al;
+            gr[R_CA] = 0.5f * gs * dx * dx;
+            gr[R_CB] = gs * dx * dy;
+            gr[R_CC] = 0.5f * gs * dy * dy;
+            gu += gs * (a.z * dx + a.w * dy);
+            gv += gs * (a.w * dx + b.x * dy);
+          }
+          gr[R_U] = gu;
+          gr[R_V] = gv;
+        }
+      }
+      if (__any_sync(kFull, contrib)) {
+        const float s = warp_reduce_scatter16(gr);
+        const int slot = lane >> 1;
+        if ((lane & 1) == 0 && slot < 15 && s != 0.f)
+          atomicAdd(grad + (int64_t)s_e[j] * kRecFloats + slot, s);
+      }
+    }
+  }
+}
+
+cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& hf, const gs_maps& maps,
+                              cudaStream_t s) {
+  const FrameDev* fd = at<FrameDev>(ws, L.frame);
+  const int block = hf.tile_w * hf.tile_h;
+  const int grid = (int)L.T;
+  if (grid == 0) return cudaSuccess;
+  switch (block) {
+    case 64: k_render_fwd<64><<<grid, 64, 0, s>>>(fd, ws, L, maps); break;
+    case 128: k_render_fwd<128><<<grid, 128, 0, s>>>(fd, ws, L, maps); break;
+    case 256: k_render_fwd<256><<<grid, 256, 0, s>>>(fd, ws, L, maps); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& hf, const gs_map_grads& g,
+                              cudaStream_t s) {
+  const FrameDev* fd = at<FrameDev>(ws, L.frame);
+  cudaError_t err = cudaMemsetAsync(at<float>(ws, L.grad2d), 0,
+                                    sizeof(float) * kRecFloats * (size_t)L.E, s);
+  if (err != cudaSuccess) return err;
+  const int block = hf.tile_w * hf.tile_h;
+  const int grid = (int)L.T;
+  if (grid == 0) return cudaSuccess;
+  switch (block) {
+    case 64: k_render_bwd<64><<<grid, 64, 0, s>>>(fd, ws, L, g); break;
+    case 128: k_render_bwd<128><<<grid, 128, 0, s>>>(fd, ws, L, g); break;
+    case 256: k_render_bwd<256><<<grid, 256, 0, s>>>(fd, ws, L, g); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gs

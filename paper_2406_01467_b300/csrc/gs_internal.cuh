@@ -1,0 +1,144 @@
+// Internal definitions shared by the libgs kernels: the device copy of a frame
+// descriptor, the workspace layout and small device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr int kRecFloats = 16;            // per-entry record / 2D-gradient slots
+constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
+constexpr int kSortThreads = 256;         // radix sort / scan block size
+constexpr int kSortItems = 16;            // items per thread
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 items per block
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+
+// Record slots (one 64-byte record per (view, Gaussian) entry).
+enum RecSlot {
+  R_U = 0, R_V = 1, R_CA = 2, R_CB = 3,      // float4 #0: centre, conic a b
+  R_CC = 4, R_O = 5, R_Z = 6, R_P0 = 7,      // float4 #1: conic c, opacity, z_c, p0
+  R_P1 = 8, R_N0 = 9, R_N1 = 10, R_N2 = 11,  // float4 #2: p1, normal
+  R_R = 12, R_G = 13, R_B = 14, R_PAD = 15   // float4 #3: colour
+};
+
+struct ViewDev {
+  float R[9];         // world->camera rotation, row-major
+  float t[3];
+  float fx, fy, cx, cy;
+  float lim[4];       // clamp bounds of x/z (lo, hi) and y/z (lo, hi) inside J
+  float campos[3];    // camera centre in world space
+  float near_plane;
+  int32_t width, height;
+  int32_t tiles_x, tiles_y;
+  int32_t scene;
+  int32_t pad_;
+};
+
+struct SceneDev {
+  const void* means;
+  const void* scales;
+  const void* quats;
+  const void* opacities;
+  const void* sh;
+  int64_t n;
+  int32_t sh_degree;
+  int32_t dtype;
+  int32_t n_views;    // views rendering this scene (1 => gradients are stored, else added)
+  int32_t pad_;
+};
+
+struct FrameDev {
+  ViewDev views[GS_MAX_VIEWS];
+  SceneDev scenes[GS_MAX_SCENES];
+  int64_t entry_off[GS_MAX_VIEWS + 1];  // entries of view v: [entry_off[v], entry_off[v+1])
+  int64_t pix_off[GS_MAX_VIEWS + 1];    // pixels of view v in the concatenated maps
+  int32_t tile_off[GS_MAX_VIEWS + 1];   // global tile ids of view v
+  int32_t n_views, n_scenes;
+  int64_t n_entries, n_pixels, pair_capacity;
+  int32_t n_tiles;
+  int32_t tile_w, tile_h, tile_shift_x, tile_shift_y;
+  float lowpass, alpha_min, alpha_max, T_min, median_T;
+  float ext_c;        // float32(2 ln(1/alpha_min))
+};
+
+// Parameter-gradient outputs, passed by value to the backward kernel.
+struct GradPtrs {
+  gs_scene_grads g[GS_MAX_SCENES];
+};
+
+struct Header {
+  unsigned long long n_vis;
+  unsigned long long n_pairs;
+  unsigned long long n_nonfinite;
+  int32_t status;
+  int32_t pad_[57];
+};
+
+// Byte offsets of every buffer inside the caller's workspace.
+struct Layout {
+  int64_t E, T, NPIX, Pcap;
+  int32_t nb_E, nb_P;       // radix blocks over entries / pairs
+  size_t hdr, frame, rec, rect, key, touched;
+  size_t vkey[2], vval[2];  // depth sort ping-pong
+  size_t pair_off;          // exclusive scan of tiles_touched in depth order
+  size_t blk;               // per-block partials of the scans
+  size_t ptile[2], pval[2]; // pair sort ping-pong
+  size_t ptile_final, pval_final;  // where the sorted pairs end up
+  size_t hist, htot;        // radix histograms [256][nb], digit totals [256]
+  size_t ranges;            // [T] int2
+  size_t px_T, px_last, px_med;
+  size_t grad2d;            // [E][16] float
+  size_t total;
+};
+
+template <typename T> __host__ __device__ inline T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+__device__ inline void set_status(Header* h, int code) {
+  atomicCAS(&h->status, 0, code);
+}
+
+__device__ inline int find_view(const int64_t* off, int n_views, int64_t e) {
+  int lo = 0, hi = n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ inline int find_view_tile(const int32_t* off, int n_views, int32_t t) {
+  int lo = 0, hi = n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T> __device__ inline float ldf(const T* p, int64_t i);
+template <> __device__ inline float ldf<float>(const float* p, int64_t i) { return __ldg(p + i); }
+template <> __device__ inline float ldf<__nv_bfloat16>(const __nv_bfloat16* p, int64_t i) {
+  return __bfloat162float(p[i]);
+}
+
+int tile_sort_bits(int64_t n_tiles);
+
+// ---- launchers (each .cu file owns its kernels) ---------------------------
+cudaError_t launch_setup(const FrameDev& fd, void* ws, const Layout& L, cudaStream_t s);
+cudaError_t launch_preprocess(void* ws, const Layout& L, const FrameDev& host_fd, cudaStream_t s);
+cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& host_fd, cudaStream_t s);
+cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& host_fd,
+                              const gs_maps& maps, cudaStream_t s);
+cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& host_fd,
+                              const gs_map_grads& g, cudaStream_t s);
+cudaError_t launch_preprocess_bwd(void* ws, const Layout& L, const FrameDev& host_fd,
+                                  const GradPtrs& gp, cudaStream_t s);
+
+}  // namespace gs
