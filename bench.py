@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the depth/normal Gaussian rasterizer: ms per forward+backward frame.
+
+One step = one pass of the whole hot path over one frame: per-Gaussian
+preprocess, binning (depth sort, pair emission, tile sort, ranges), compositing
+forward (colour, alpha, median planar depth, normal), compositing backward and
+preprocess backward down to the parameter gradients.
+
+Default workload: the unbounded synthetic scene (3M Gaussians, SH degree 3,
+1297x840 pinhole view, FP32), seeded; inputs are larger than L2, so no flush
+is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank renders its own replica of the frame (the path needs
+no exchange between ranks); ``value`` is the max-over-ranks step time.  The
+``reference`` arm times the FP64 CPU oracle on a bounded sample of the same
+frame and extrapolates to a whole frame.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms per fwd+bwd frame (colour+depth+normal) at 3M Gaussians, 1297x840"
+PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}
+N_SM, FP32_LANES = 148, 128
+
+CONFIGS = {
+    "unbounded": dict(workload="unbounded scene, 3M Gaussians, SH deg 3, 1297x840, FP32, fwd+bwd",
+                      n=3_000_000, seed=2),
+    "object": dict(workload="object scene, 200K Gaussians, SH deg 3, 800x600, FP32, fwd+bwd",
+                   n=200_000, seed=1),
+    "tiny": dict(workload="tiny scene, 2000 Gaussians, SH deg 0, 128x128, FP32, fwd+bwd", n=2000, seed=0),
+}
+
+
+def make_workload(name):
+    from paper_2406_01467_b300 import scenes
+    c = CONFIGS[name]
+    if name == "unbounded":
+        return scenes.unbounded_scene(c["n"], c["seed"]), scenes.unbounded_camera()
+    if name == "object":
+        return scenes.object_scene(c["n"], c["seed"]), scenes.object_camera()
+    return scenes.tiny_scene(c["n"], c["seed"]), scenes.tiny_camera()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while it runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self, max_mhz_default):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": max_mhz_default, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def launches_per_step(n_tiles, n_dtypes=1):
+    """Kernels libgs launches for one preprocess + bin + fwd + bwd (memsets excluded)."""
+    bits = max(1, int(np.ceil(np.log2(max(n_tiles, 2)))))
+    tile_passes = (bits + 7) // 8
+    setup, pre = 1, n_dtypes
+    binning = 3 + 4 * 3 + 2 + 1 + 3 * tile_passes + 1
+    return setup + pre + binning + 1 + 1 + n_dtypes
+
+
+# --------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------
+def run_ours(args, rank, world, device):
+    import torch
+    from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, scenes
+
+    torch.cuda.set_device(device)
+    scene, cam = make_workload(args.config)
+    st = SceneTensors.from_scene(scene, device)
+    params = RenderParams()
+    frame = Frame([st], [(cam, 0)], params)
+    frame.forward(sync_capacity=True)
+    s0 = frame.stats()
+    # capacity with margin, then no host synchronisation inside the timed region
+    need = int(s0.n_pairs)
+    if frame.pair_capacity < need * 1.1:
+        frame._alloc(int(need * 1.25) + 1024)
+    up = [torch.from_numpy(u[0]).to(device) for u in scenes.upstream_grads(11, cam.height, cam.width)]
+    grads = frame.alloc_grads()
+
+    n_ev = 6
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record()
+        frame.preprocess()
+        if ev is not None:
+            ev[1].record()
+        frame.bin()
+        if ev is not None:
+            ev[2].record()
+        frame.render()
+        frame.backward(*up, grads=grads, split=True, events=ev[3:6] if ev is not None else None)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stats = frame.stats()
+    if frame.last_status != 0:
+        raise RuntimeError(f"device status {frame.last_status} after warm-up")
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    with sampler:
+        t0.record()
+        for k in range(args.steps):
+            step(evs[k])
+        t1.record()
+        torch.cuda.synchronize()
+    ms_total = t0.elapsed_time(t1)
+    if dist:
+        tdist.barrier()
+    frame.stats()
+    if frame.last_status != 0:
+        raise RuntimeError(f"device status {frame.last_status} after the timed steps")
+    stages = {"preprocess": 0.0, "bin": 0.0, "render_fwd": 0.0, "composite_bwd": 0.0, "preprocess_bwd": 0.0}
+    for ev in evs:
+        stages["preprocess"] += ev[0].elapsed_time(ev[1])
+        stages["bin"] += ev[1].elapsed_time(ev[2])
+        stages["render_fwd"] += ev[2].elapsed_time(ev[3])
+        stages["composite_bwd"] += ev[3].elapsed_time(ev[4])
+        stages["preprocess_bwd"] += ev[4].elapsed_time(ev[5])
+    stages = {k: v / args.steps for k, v in stages.items()}
+    ms = ms_total / args.steps
+    if dist:
+        t = torch.tensor([ms], device=device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end: host parameters in, host maps and gradients out --------------------
+    e2e = None
+    if not args.no_e2e:
+        host = {k: getattr(st, k).detach().cpu().pin_memory() for k in ("means", "scales", "quats", "opacities", "sh")}
+        outs = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in
+                (("color", frame.color), ("alpha", frame.alpha), ("depth", frame.depth), ("normal", frame.normal))}
+        gouts = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in grads[0].items()}
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = sum(v.numel() * v.element_size() for v in outs.values()) + \
+            sum(v.numel() * v.element_size() for v in gouts.values())
+
+        def e2e_step():
+            for k, v in host.items():
+                getattr(st, k).copy_(v, non_blocking=True)
+            step()
+            for k, v in outs.items():
+                v.copy_(getattr(frame, k), non_blocking=True)
+            for k, v in gouts.items():
+                v.copy_(grads[0][k], non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        n_e2e = max(3, min(args.steps, 20))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n_e2e):
+            e2e_step()
+        b.record()
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / n_e2e
+        if dist:
+            t = torch.tensor([e2e_ms], device=device)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
+
+    # ---- roofline ---------------------------------------------------------------------------
+    peaks, src = load_peaks()
+    clocks = sampler.summary(peaks.get("sm_max_mhz", 2032.0))
+    K = (scene.sh_degree + 1) ** 2
+    N = scene.n
+    pbytes = 4 * (3 + 3 + 4 + 1 + 3 * K)
+    nvis, P = int(stats.n_visible), int(stats.n_pairs)
+    ev_f, ev_b = int(stats.n_evals_fwd), int(stats.n_evals_bwd)
+    hbm = peaks["hbm_gbs"]
+    alu_peak = N_SM * FP32_LANES * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # T lane-ops/s
+    OPS_FWD, OPS_BWD = 20, 55
+    algo = {
+        # bytes: every parameter read, record + rect + key + count written
+        "preprocess": ("hbm", N * pbytes + nvis * 64 + N * 16),
+        # bytes: per pair one read and one write per sort pass lower bound (24 B), depth keys
+        "bin": ("hbm", P * 24 + nvis * 16 + N * 8),
+        "render_fwd": ("alu", ev_f * OPS_FWD),
+        "composite_bwd": ("alu", ev_b * OPS_BWD),
+        # bytes: parameters + 2D gradients of visible entries read, all parameter gradients written
+        "preprocess_bwd": ("hbm", nvis * (pbytes + 64) + N * pbytes),
+    }
+    roof = {}
+    for k, (bound, work) in algo.items():
+        t_s = stages[k] * 1e-3
+        if bound == "hbm":
+            ach = work / t_s / 1e9
+            roof[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                       "frac": round(ach / hbm, 4), "bytes": int(work), "ms": round(stages[k], 4)}
+        else:
+            ach = work / t_s / 1e12
+            roof[k] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
+                       "unit": "Tops/s", "frac": round(ach / alu_peak, 4), "ops": int(work),
+                       "ms": round(stages[k], 4)}
+    dom = max(stages, key=lambda k: stages[k])
+    r = dict(roof[dom])
+    r["kernel"] = dom
+    r["traffic"] = None
+    r["peak_source"] = f"{src} ({'MEASURED_PEAKS.json' if src == 'measured' else 'recipe fallback'})"
+    out = {
+        "metric": METRIC, "value": round(ms, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": CONFIGS[args.config]["workload"], "gaussians": N,
+                   "image": f"{cam.width}x{cam.height}", "tile": f"{params.tile_w}x{params.tile_h}",
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+        "roofline": r, "stages": roof,
+        "counts": {"visible": nvis, "pairs": P, "evals_fwd": ev_f, "evals_bwd": ev_b},
+        "clocks": clocks, "e2e": e2e,
+        "gpu_launches": launches_per_step(frame_tiles(cam, params)) * args.steps,
+    }
+    return out
+
+
+def frame_tiles(cam, p):
+    return ((cam.width + p.tile_w - 1) // p.tile_w) * ((cam.height + p.tile_h - 1) // p.tile_h)
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle (baseline arm and cpu_baseline field)
+# --------------------------------------------------------------------------------------
+def oracle_sample(scene, cam, crop=32, n_crops=1, seed=0):
+    """Time the FP64 oracle on a bounded sample: its FP32 binning decisions over
+    all Gaussians, then forward + gradients for ``n_crops`` crops of crop x crop
+    pixels restricted to the Gaussians whose rectangles reach them.  Returns the
+    estimated ms for a whole frame and the measured seconds."""
+    import torch
+    import oracle
+    from oracle import binning
+    from paper_2406_01467_b300 import scenes
+
+    p = oracle.RenderParams()
+    f32 = lambda x: float(np.float32(x))
+    p = oracle.RenderParams(lowpass=f32(p.lowpass), alpha_min=f32(p.alpha_min), alpha_max=f32(p.alpha_max),
+                            T_min=f32(p.T_min), median_T=f32(p.median_T), clamp_margin=f32(p.clamp_margin))
+    t0 = time.perf_counter()
+    dec = binning.decide(scene.means, scene.scales, scene.quats, scene.opacities, cam, p)
+    t_dec = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    t_crop = 0.0
+    up = [u[0] for u in scenes.upstream_grads(11, cam.height, cam.width)]
+    for _ in range(n_crops):
+        x0 = int(rng.integers(0, cam.width - crop))
+        y0 = int(rng.integers(0, cam.height - crop))
+        r = dec["rect"]
+        sel = dec["valid"] & (r[:, 1] >= x0) & (r[:, 0] < x0 + crop) & (r[:, 3] >= y0) & (r[:, 2] < y0 + crop)
+        sub = scene.subset(np.nonzero(sel)[0])
+        ys, xs = np.mgrid[y0:y0 + crop, x0:x0 + crop]
+        pix = (ys * cam.width + xs).reshape(-1)
+        t1 = time.perf_counter()
+        oracle.render_grads(sub, cam, up, p, pixels=pix)
+        t_crop += time.perf_counter() - t1
+    npix = cam.width * cam.height
+    est_ms = (t_dec + t_crop / (n_crops * crop * crop) * npix) * 1e3
+    return est_ms, t_dec + t_crop, torch.get_num_threads(), \
+        f"FP32 binning of all {scene.n} Gaussians + fwd/grad of {n_crops} crop(s) of {crop}x{crop} px, " \
+        f"scaled by {npix}/{n_crops * crop * crop} pixels"
+
+
+def run_reference(args, world):
+    scene, cam = make_workload(args.config)
+    for _ in range(args.warmup):
+        oracle_sample(scene, cam, seed=1000 + _)
+    vals, secs = [], 0.0
+    for k in range(args.steps):
+        est, s, cores, sample = oracle_sample(scene, cam, seed=k)
+        vals.append(est)
+        secs += s
+    v = float(np.mean(vals))
+    out = {
+        "metric": METRIC, "value": round(v, 2), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(v, 2), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": CONFIGS[args.config]["workload"], "gaussians": scene.n,
+                   "image": f"{cam.width}x{cam.height}", "parallelism": "cpu"},
+        "cpu_baseline": {"value": round(v, 2), "unit": "ms", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(v, 2), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=list(CONFIGS), default="unbounded")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args, world)), flush=True)
+        return 0
+
+    import torch
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    out = run_ours(args, rank, world, f"cuda:{local}")
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        scene, cam = make_workload(args.config)
+        est, secs, cores, sample = oracle_sample(scene, cam, n_crops=16)
+        out["cpu_baseline"] = {"value": round(est, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+                               "sample": sample, "seconds": round(secs, 1)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -133,6 +133,8 @@ typedef struct {
   int64_t n_visible;    /* entries that touch at least one pixel */
   int64_t n_pairs;      /* (tile, Gaussian) pairs needed */
   int64_t n_nonfinite;  /* entries culled for non-finite inputs */
+  int64_t n_evals_fwd;  /* (pixel, splat) evaluations of the last gs_render_fwd */
+  int64_t n_evals_bwd;  /* (pixel, splat) evaluations of the last gs_composite_bwd */
   int32_t status;       /* sticky gs_status of the device work */
 } gs_stats;
 
@@ -160,9 +162,20 @@ gs_status gs_render_fwd(const gs_frame* frame, const gs_maps* maps, void* stream
 
 /* Backward of gs_render_fwd and of gs_preprocess: replays each pixel back to
  * front and writes dL/d(means, scales, quats, opacities, sh) for every scene
- * (`grads` is a host array [n_scenes]). */
+ * (`grads` is a host array [n_scenes]).  Equivalent to gs_composite_bwd
+ * followed by gs_preprocess_bwd. */
 gs_status gs_render_bwd(const gs_frame* frame, const gs_map_grads* dmaps,
                         const gs_scene_grads* grads, void* stream);
+
+/* First half of gs_render_bwd: the compositing backward (back-to-front replay
+ * of Eq. 3, Eq. 4 and the normal blend) into per-entry gradients of the
+ * projected quantities (kept in the workspace). */
+gs_status gs_composite_bwd(const gs_frame* frame, const gs_map_grads* dmaps, void* stream);
+
+/* Second half of gs_render_bwd: chain rule of the per-Gaussian stage (Eq. 1-2,
+ * 8-22 and the SH colour) from the workspace's per-entry gradients to the
+ * parameters.  Buffers of scenes seen by several views are zeroed, then summed. */
+gs_status gs_preprocess_bwd(const gs_frame* frame, const gs_scene_grads* grads, void* stream);
 
 /* Intermediate results for tests and tools, copied to caller device buffers on
  * `stream`; any pointer may be NULL.  rec: [n_entries][16] FP32 per-entry

@@ -62,11 +62,13 @@ class GsSceneGrads(Structure):
 
 class GsStats(Structure):
     _fields_ = [("n_entries", c_int64), ("n_visible", c_int64), ("n_pairs", c_int64),
-                ("n_nonfinite", c_int64), ("status", c_int32)]
+                ("n_nonfinite", c_int64), ("n_evals_fwd", c_int64), ("n_evals_bwd", c_int64),
+                ("status", c_int32)]
 
 
 EXPORTS = ("gs_workspace_size", "gs_preprocess", "gs_bin", "gs_render_fwd", "gs_render_bwd",
-           "gs_debug_copy", "gs_check", "gs_last_error_string")
+           "gs_composite_bwd", "gs_preprocess_bwd", "gs_debug_copy", "gs_check",
+           "gs_last_error_string")
 
 _lib = None
 
@@ -96,6 +98,10 @@ def load(path: str = LIB_PATH):
     lib.gs_render_fwd.restype = c_int32
     lib.gs_render_bwd.argtypes = [pf, POINTER(GsMapGrads), POINTER(GsSceneGrads), c_void_p]
     lib.gs_render_bwd.restype = c_int32
+    lib.gs_composite_bwd.argtypes = [pf, POINTER(GsMapGrads), c_void_p]
+    lib.gs_composite_bwd.restype = c_int32
+    lib.gs_preprocess_bwd.argtypes = [pf, POINTER(GsSceneGrads), c_void_p]
+    lib.gs_preprocess_bwd.restype = c_int32
     lib.gs_debug_copy.argtypes = [pf, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p]
     lib.gs_debug_copy.restype = c_int32

@@ -243,13 +243,23 @@ gs_status gs_render_fwd(const gs_frame* frame, const gs_maps* maps, void* stream
   return GS_OK;
 }
 
-gs_status gs_render_bwd(const gs_frame* frame, const gs_map_grads* dmaps, const gs_scene_grads* grads,
-                        void* stream) {
+gs_status gs_composite_bwd(const gs_frame* frame, const gs_map_grads* dmaps, void* stream) {
   FrameDev fd;
   Layout L;
   gs_status st = prepare_ws(frame, fd, L);
   if (st != GS_OK) return st;
-  if (!dmaps || !grads) return fail(GS_ERR_INVALID_ARG, "dmaps and grads must not be NULL");
+  if (!dmaps) return fail(GS_ERR_INVALID_ARG, "dmaps must not be NULL");
+  cudaError_t e = launch_render_bwd(frame->workspace, L, fd, *dmaps, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "composite_bwd");
+  return GS_OK;
+}
+
+gs_status gs_preprocess_bwd(const gs_frame* frame, const gs_scene_grads* grads, void* stream) {
+  FrameDev fd;
+  Layout L;
+  gs_status st = prepare_ws(frame, fd, L);
+  if (st != GS_OK) return st;
+  if (!grads) return fail(GS_ERR_INVALID_ARG, "grads must not be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   GradPtrs gp;
   memset(&gp, 0, sizeof(gp));
@@ -268,11 +278,17 @@ gs_status gs_render_bwd(const gs_frame* frame, const gs_map_grads* dmaps, const 
     }
   }
   if (e != cudaSuccess) return cuda_fail(e, "zeroing gradients");
-  e = launch_render_bwd(frame->workspace, L, fd, *dmaps, s);
-  if (e != cudaSuccess) return cuda_fail(e, "render_bwd");
   e = launch_preprocess_bwd(frame->workspace, L, fd, gp, s);
   if (e != cudaSuccess) return cuda_fail(e, "preprocess_bwd");
   return GS_OK;
+}
+
+gs_status gs_render_bwd(const gs_frame* frame, const gs_map_grads* dmaps, const gs_scene_grads* grads,
+                        void* stream) {
+  if (!dmaps || !grads) return fail(GS_ERR_INVALID_ARG, "dmaps and grads must not be NULL");
+  gs_status st = gs_composite_bwd(frame, dmaps, stream);
+  if (st != GS_OK) return st;
+  return gs_preprocess_bwd(frame, grads, stream);
 }
 
 gs_status gs_debug_copy(const gs_frame* frame, float* rec, int32_t* rect, int32_t* pair_tile,
@@ -318,6 +334,8 @@ gs_status gs_check(const gs_frame* frame, gs_stats* out, void* stream) {
     out->n_visible = (int64_t)h.n_vis;
     out->n_pairs = (int64_t)h.n_pairs;
     out->n_nonfinite = (int64_t)h.n_nonfinite;
+    out->n_evals_fwd = (int64_t)h.n_evals_fwd;
+    out->n_evals_bwd = (int64_t)h.n_evals_bwd;
     out->status = h.status;
   }
   if (h.status == GS_ERR_CAPACITY)

@@ -22,6 +22,12 @@ namespace gs {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// Adds the block's evaluation count to a header counter (one atomic per warp).
+__device__ inline void count_evals(uint32_t n, unsigned long long* counter) {
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(kFull, n, o);
+  if ((threadIdx.x & 31) == 0 && n) atomicAdd(counter, (unsigned long long)n);
+}
+
 struct TileCtx {
   int view, px, py, W, H;
   bool inside;
@@ -64,6 +70,7 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, depth = 0.f;
   int last = -1, med = -1;
   bool done = !c.inside;
+  uint32_t evals = 0;
   for (int b0 = range.x; b0 < range.y; b0 += BLOCK) {
     if (__syncthreads_count(done) == BLOCK) break;
     const int i = b0 + threadIdx.x;
@@ -77,6 +84,7 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     __syncthreads();
     const int nb = min(BLOCK, range.y - b0);
     for (int j = 0; !done && j < nb; ++j) {
+      ++evals;
       const float4 a = s_a[j], b = s_b[j];
       const float dx = a.x - fpx, dy = a.y - fpy;
       const float sig = 0.5f * (a.z * dx * dx + b.x * dy * dy) + a.w * dx * dy;
@@ -96,6 +104,7 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
       T = Tn;
     }
   }
+  count_evals(evals, &at<Header>(ws, L.hdr)->n_evals_fwd);
   if (!c.inside) return;
   if (med < 0 && last >= 0) {   // median never reached: depth of the last contributor
     med = last;
@@ -199,6 +208,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
 
   float T = Tf;
   float Sc[3] = {0.f, 0.f, 0.f}, Sn[3] = {0.f, 0.f, 0.f};
+  uint32_t evals = 0;
   for (int b1 = end; b1 > range.x; b1 -= BLOCK) {
     const int b0 = max(range.x, b1 - BLOCK);
     __syncthreads();
@@ -221,6 +231,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
       for (int k = 0; k < 16; ++k) gr[k] = 0.f;
       bool contrib = false;
       if (idx <= last) {
+        ++evals;
         const float4 a = s_a[j], b = s_b[j];
         const float dx = a.x - fpx, dy = a.y - fpy;
         const float sig = 0.5f * (a.z * dx * dx + b.x * dy * dy) + a.w * dx * dy;
@@ -273,11 +284,14 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
       }
     }
   }
+  count_evals(evals, &at<Header>(ws, L.hdr)->n_evals_bwd);
 }
 
 cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& hf, const gs_maps& maps,
                               cudaStream_t s) {
   const FrameDev* fd = at<FrameDev>(ws, L.frame);
+  cudaError_t err = cudaMemsetAsync(&at<Header>(ws, L.hdr)->n_evals_fwd, 0, 8, s);
+  if (err != cudaSuccess) return err;
   const int block = hf.tile_w * hf.tile_h;
   const int grid = (int)L.T;
   if (grid == 0) return cudaSuccess;
@@ -295,6 +309,7 @@ cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& hf, con
   const FrameDev* fd = at<FrameDev>(ws, L.frame);
   cudaError_t err = cudaMemsetAsync(at<float>(ws, L.grad2d), 0,
                                     sizeof(float) * kRecFloats * (size_t)L.E, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(&at<Header>(ws, L.hdr)->n_evals_bwd, 0, 8, s);
   if (err != cudaSuccess) return err;
   const int block = hf.tile_w * hf.tile_h;
   const int grid = (int)L.T;

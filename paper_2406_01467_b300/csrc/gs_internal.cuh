@@ -75,8 +75,10 @@ struct Header {
   unsigned long long n_vis;
   unsigned long long n_pairs;
   unsigned long long n_nonfinite;
+  unsigned long long n_evals_fwd;
+  unsigned long long n_evals_bwd;
   int32_t status;
-  int32_t pad_[57];
+  int32_t pad_[53];
 };
 
 // Byte offsets of every buffer inside the caller's workspace.

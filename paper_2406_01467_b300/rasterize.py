@@ -205,8 +205,12 @@ class Frame:
                             sh=torch.empty(tuple(s.sh.shape), **f32)))
         return out
 
-    def backward(self, dcolor=None, dalpha=None, ddepth=None, dnormal=None, grads=None, stream=None):
-        """Enqueue the backward pass; returns per-scene FP32 gradient dicts."""
+    def backward(self, dcolor=None, dalpha=None, ddepth=None, dnormal=None, grads=None, stream=None,
+                 split: bool = False, events=None):
+        """Enqueue the backward pass; returns per-scene FP32 gradient dicts.
+
+        ``split`` issues it as gs_composite_bwd + gs_preprocess_bwd; ``events``
+        (three CUDA events) are then recorded before, between and after the two."""
         def flat(t, n):
             if t is None:
                 return None
@@ -224,8 +228,21 @@ class Frame:
         for i, g in enumerate(grads):
             cg[i] = GsSceneGrads(_ptr(g["means"]), _ptr(g["scales"]), _ptr(g["quats"]),
                                  _ptr(g["opacities"]), _ptr(g["sh"]))
-        check(self.lib.gs_render_bwd(ctypes.byref(self.frame), ctypes.byref(mg), cg, _stream(stream)),
-              "gs_render_bwd")
+        self._cg, self._mg = cg, mg
+        if not split:
+            check(self.lib.gs_render_bwd(ctypes.byref(self.frame), ctypes.byref(mg), cg, _stream(stream)),
+                  "gs_render_bwd")
+            return grads
+        if events:
+            events[0].record()
+        check(self.lib.gs_composite_bwd(ctypes.byref(self.frame), ctypes.byref(mg), _stream(stream)),
+              "gs_composite_bwd")
+        if events:
+            events[1].record()
+        check(self.lib.gs_preprocess_bwd(ctypes.byref(self.frame), cg, _stream(stream)),
+              "gs_preprocess_bwd")
+        if events:
+            events[2].record()
         return grads
 
     # ------------------------------------------------------------------
