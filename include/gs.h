@@ -80,7 +80,8 @@ typedef struct {
 
 /* Render parameters; the paper keeps the 3D GS defaults (Sec. 4.1.1). */
 typedef struct {
-  int32_t tile_w, tile_h; /* tile size; tile_w * tile_h must be 64, 128 or 256 */
+  int32_t tile_w, tile_h; /* tile size: powers of two, tile_w >= 8, tile_h >= 4,
+                             tile_w * tile_h in {64, 128, 256} */
   float lowpass;          /* px^2 added to the 2x2 screen covariance, >= 0 */
   float alpha_min;        /* in (0, 1): splats below it are skipped at a pixel */
   float alpha_max;        /* in [alpha_min, 1): alpha clamp */
@@ -180,7 +181,8 @@ gs_status gs_preprocess_bwd(const gs_frame* frame, const gs_scene_grads* grads, 
 /* Intermediate results for tests and tools, copied to caller device buffers on
  * `stream`; any pointer may be NULL.  rec: [n_entries][16] FP32 per-entry
  * records (u, v, conic a b c, opacity, z, p0 | p1, n0 n1 n2, r g b, spare);
- * rect: [n_entries][4] int32 pixel rectangle (i0, i1, j0, j1), (0,-1,0,-1)
+ * (the spare slot holds ln(o / alpha_min) plus a margin: the sigma beyond which a
+ * splat cannot reach alpha_min); rect: [n_entries][4] int32 pixel rectangle (i0, i1, j0, j1), (0,-1,0,-1)
  * when culled; pair_tile/pair_entry: [pair_capacity] int32 sorted pairs;
  * ranges: [total tiles][2] int32.  grad2d: [n_entries][16] FP32 dL/d(record),
  * valid after gs_render_bwd. */

@@ -18,7 +18,8 @@ not describe binning; it inherits it from 3D GS (Sec. 4.1.1).  The order is:
  8. ex = sqrt(C A00), ey = sqrt(C A11), C = float32(2 ln(1/alpha_min)): the
     axis-aligned box of the ellipse on which alpha = alpha_min for opacity 1.
  9. xlo = (u - ex) - 0.5, xhi = (u + ex) - 0.5 (same for y); invalid unless
-    xhi >= 0, xlo <= W-1, yhi >= 0, ylo <= H-1 and the opacity is > 0.
+    xhi >= 0, xlo <= W-1, yhi >= 0, ylo <= H-1 and opacity >= alpha_min (a splat
+    whose opacity is below alpha_min can never reach it, since alpha <= opacity).
 10. pixel rect i0 = max(0, ceil xlo), i1 = min(W-1, floor xhi) (same for j);
     invalid if empty.  Tile rect = pixel rect // tile size.
 11. sort key: (tile id, float bits of z, Gaussian id), ascending.
@@ -89,7 +90,7 @@ def decide(means, scales, quats, opacities, cam, params: RenderParams):
         ylo = (v - ey) - half
         yhi = (v + ey) - half
         valid &= (xhi >= 0) & (xlo <= F(W - 1)) & (yhi >= 0) & (ylo <= F(H - 1))
-        valid &= o > 0
+        valid &= o >= F(params.alpha_min)
         i0 = np.where(valid, np.maximum(F(0), np.ceil(xlo)), 0).astype(np.int64)
         i1 = np.where(valid, np.minimum(F(W - 1), np.floor(xhi)), -1).astype(np.int64)
         j0 = np.where(valid, np.maximum(F(0), np.ceil(ylo)), 0).astype(np.int64)

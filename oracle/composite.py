@@ -113,7 +113,7 @@ def composite(pre, dec, width, height, params: RenderParams, pixels=None):
     alpha = torch.clamp(alpha_raw, max=params.alpha_max)
 
     with torch.no_grad():
-        keep = vmask & (alpha >= params.alpha_min) & (sigma >= 0)
+        keep = vmask & (alpha >= params.alpha_min)
         a_eff = torch.where(keep, alpha, torch.zeros_like(alpha))
         T_incl = torch.cumprod(1.0 - a_eff, dim=1)
         included = keep & (T_incl >= params.T_min)

@@ -42,8 +42,9 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   const gs_params& p = f->params;
   const int sx = log2_exact(p.tile_w), sy = log2_exact(p.tile_h);
   const int block = p.tile_w * p.tile_h;
-  if (sx < 0 || sy < 0 || !(block == 64 || block == 128 || block == 256))
-    return fail(GS_ERR_INVALID_ARG, "tile %dx%d: sides must be powers of two with 64, 128 or 256 pixels",
+  if (sx < 0 || sy < 0 || p.tile_w < 8 || p.tile_h < 4 || !(block == 64 || block == 128 || block == 256))
+    return fail(GS_ERR_INVALID_ARG,
+                "tile %dx%d: sides must be powers of two, width >= 8, height >= 4, 64, 128 or 256 pixels",
                 p.tile_w, p.tile_h);
   if (!(p.lowpass >= 0.f) || !std::isfinite(p.lowpass))
     return fail(GS_ERR_INVALID_ARG, "lowpass must be finite and >= 0");
@@ -74,7 +75,7 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
     d.n = s.n; d.sh_degree = s.sh_degree; d.dtype = s.dtype;
   }
   int64_t E = 0, NPIX = 0;
-  int64_t T = 0;
+  int64_t T = 0, NCH = 0;
   for (int v = 0; v < f->n_views; ++v) {
     const gs_view& cv = f->views[v];
     if (cv.scene < 0 || cv.scene >= f->n_scenes) return fail(GS_ERR_INVALID_ARG, "view %d: bad scene index", v);
@@ -111,6 +112,8 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
     fd.entry_off[v] = E;
     fd.pix_off[v] = NPIX;
     fd.tile_off[v] = (int32_t)T;
+    fd.chunk_off[v] = (int32_t)NCH;
+    NCH += (f->scenes[cv.scene].n + 127) / 128;
     E += f->scenes[cv.scene].n;
     NPIX += (int64_t)cv.width * cv.height;
     T += (int64_t)V.tiles_x * V.tiles_y;
@@ -118,6 +121,8 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   fd.entry_off[f->n_views] = E;
   fd.pix_off[f->n_views] = NPIX;
   fd.tile_off[f->n_views] = (int32_t)T;
+  fd.chunk_off[f->n_views] = (int32_t)NCH;
+  fd.n_chunks = (int32_t)NCH;
   if (E >= (int64_t(1) << 31)) return fail(GS_ERR_INVALID_ARG, "too many (view, Gaussian) entries: %lld", (long long)E);
   if (T >= (int64_t(1) << 31)) return fail(GS_ERR_INVALID_ARG, "too many tiles");
   fd.n_entries = E;

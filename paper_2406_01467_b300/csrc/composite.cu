@@ -9,7 +9,15 @@
 //   depth = z_c + p Delta (Eq. 4) of the first splat with T' <= median_T
 //   (the median depth of Sec. 1), else of the last contributor;
 //   alpha map = 1 - T_final.
-// The block leaves the loop as soon as every pixel of the tile is done.
+//
+// Each warp owns an 8x4 block of the tile's pixels.  When a batch of records is
+// staged, the thread that loads a record also finds which warps' blocks the
+// splat can reach: the minimum of sigma over the block's rectangle of pixel
+// centres (exact, over its four edges) against sigma_cut = ln(o / alpha_min)
+// with a small safety margin.  A warp walks only the records whose bit it owns,
+// so a splat it skips is one every one of its pixels would have skipped by the
+// alpha test: the maps are the same as without the culling.  The block leaves
+// the loop as soon as every pixel of the tile is done.
 //
 // Backward replays each pixel from its last contributor toward the front,
 // recovering T by division (alpha <= alpha_max < 1) and the colour / normal
@@ -21,8 +29,9 @@
 namespace gs {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kSubW = 8, kSubH = 4;  // pixels of one warp's block
 
-// Adds the block's evaluation count to a header counter (one atomic per warp).
+// Adds the warp's evaluation count to a header counter (one atomic per warp).
 __device__ inline void count_evals(uint32_t n, unsigned long long* counter) {
   for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(kFull, n, o);
   if ((threadIdx.x & 31) == 0 && n) atomicAdd(counter, (unsigned long long)n);
@@ -30,10 +39,11 @@ __device__ inline void count_evals(uint32_t n, unsigned long long* counter) {
 
 struct TileCtx {
   int view, px, py, W, H;
+  int x0, y0;          // first pixel of the tile
   bool inside;
-  int64_t pix;        // global pixel index (concatenated views)
-  int64_t pix_local;  // index inside the view
-  int64_t pix_base;   // first pixel of the view
+  int64_t pix;         // global pixel index (concatenated views)
+  int64_t pix_local;   // index inside the view
+  int64_t pix_base;    // first pixel of the view
 };
 
 __device__ inline TileCtx tile_ctx(const FrameDev* fd, int tile) {
@@ -42,8 +52,12 @@ __device__ inline TileCtx tile_ctx(const FrameDev* fd, int tile) {
   const ViewDev& V = fd->views[c.view];
   const int local = tile - fd->tile_off[c.view];
   const int tx = local % V.tiles_x, ty = local / V.tiles_x;
-  c.px = tx * fd->tile_w + (int)(threadIdx.x % fd->tile_w);
-  c.py = ty * fd->tile_h + (int)(threadIdx.x / fd->tile_w);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub_per_row = fd->tile_w / kSubW;
+  c.x0 = tx * fd->tile_w;
+  c.y0 = ty * fd->tile_h;
+  c.px = c.x0 + (warp % sub_per_row) * kSubW + (lane % kSubW);
+  c.py = c.y0 + (warp / sub_per_row) * kSubH + (lane / kSubW);
   c.W = V.width;
   c.H = V.height;
   c.inside = c.px < c.W && c.py < c.H;
@@ -53,10 +67,60 @@ __device__ inline TileCtx tile_ctx(const FrameDev* fd, int tile) {
   return c;
 }
 
+// sigma at offset (dx, dy) from the centre.
+__device__ inline float quad(float a, float b, float c, float dx, float dy) {
+  return 0.5f * (a * dx * dx + c * dy * dy) + b * dx * dy;
+}
+
+// Minimum of sigma over the rectangle [X0, X1] x [Y0, Y1] (pixel-centre
+// coordinates): zero if the centre is inside, else the least of the four
+// edges' minima (each a 1D convex quadratic, clamped to the edge).
+__device__ inline float rect_min_sigma(float u, float v, float a, float b, float c, float ia,
+                                       float ic, float X0, float X1, float Y0, float Y1) {
+  if (u >= X0 && u <= X1 && v >= Y0 && v <= Y1) return 0.f;
+  float best = 3.4e38f;
+  // vertical edges x = X: dx fixed, dy minimises c dy + b dx = 0
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float X = e ? X1 : X0;
+    const float dx = u - X;
+    const float y = fminf(fmaxf(v + b * dx * ic, Y0), Y1);
+    best = fminf(best, quad(a, b, c, dx, v - y));
+  }
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float Y = e ? Y1 : Y0;
+    const float dy = v - Y;
+    const float x = fminf(fmaxf(u + b * dy * ia, X0), X1);
+    best = fminf(best, quad(a, b, c, u - x, dy));
+  }
+  return best;
+}
+
+// Bit w set: the splat can reach a pixel of warp w's block.
+template <int NWARPS>
+__device__ inline uint32_t warp_mask(const float4& r0, const float4& r1, const float4& r3,
+                                     int x0, int y0, int sub_per_row) {
+  const float u = r0.x, v = r0.y, a = r0.z, b = r0.w, c = r1.x;
+  const float cut = r3.w;
+  const float ia = 1.f / a, ic = 1.f / c;
+  uint32_t m = 0;
+#pragma unroll
+  for (int w = 0; w < NWARPS; ++w) {
+    const float X0 = (float)(x0 + (w % sub_per_row) * kSubW) + 0.5f;
+    const float Y0 = (float)(y0 + (w / sub_per_row) * kSubH) + 0.5f;
+    if (rect_min_sigma(u, v, a, b, c, ia, ic, X0, X0 + (kSubW - 1), Y0, Y0 + (kSubH - 1)) <= cut)
+      m |= 1u << w;
+  }
+  return m;
+}
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_maps maps) {
+  constexpr int NW = BLOCK / 32;
   __shared__ float4 s_a[BLOCK], s_b[BLOCK], s_c[BLOCK], s_d[BLOCK];
+  __shared__ uint32_t s_m[BLOCK];
   const Header* hdr = at<Header>(ws, L.hdr);
   if (hdr->status == GS_ERR_CAPACITY) return;
   const int tile = blockIdx.x;
@@ -66,6 +130,9 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
   const float4* rec = at<float4>(ws, L.rec);
   const float amin = fd->alpha_min, amax = fd->alpha_max, tmin = fd->T_min, tmed = fd->median_T;
   const float fpx = c.px + 0.5f, fpy = c.py + 0.5f;
+  const int lane = threadIdx.x & 31;
+  const uint32_t wbit = 1u << (threadIdx.x >> 5);
+  const int sub_per_row = fd->tile_w / kSubW;
 
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, depth = 0.f;
   int last = -1, med = -1;
@@ -76,32 +143,42 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     const int i = b0 + threadIdx.x;
     if (i < range.y) {
       const float4* r = rec + 4 * (int64_t)pval[i];
-      s_a[threadIdx.x] = r[0];
-      s_b[threadIdx.x] = r[1];
-      s_c[threadIdx.x] = r[2];
-      s_d[threadIdx.x] = r[3];
+      const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3];
+      s_a[threadIdx.x] = r0;
+      s_b[threadIdx.x] = r1;
+      s_c[threadIdx.x] = r2;
+      s_d[threadIdx.x] = r3;
+      s_m[threadIdx.x] = warp_mask<NW>(r0, r1, r3, c.x0, c.y0, sub_per_row);
     }
     __syncthreads();
     const int nb = min(BLOCK, range.y - b0);
-    for (int j = 0; !done && j < nb; ++j) {
-      ++evals;
-      const float4 a = s_a[j], b = s_b[j];
-      const float dx = a.x - fpx, dy = a.y - fpy;
-      const float sig = 0.5f * (a.z * dx * dx + b.x * dy * dy) + a.w * dx * dy;
-      const float al = fminf(amax, b.y * __expf(-sig));
-      if (sig < 0.f || al < amin) continue;
-      const float Tn = T * (1.f - al);
-      if (Tn < tmin) { done = true; break; }
-      const float w = al * T;
-      const float4 cc = s_c[j], d = s_d[j];
-      C0 += w * d.x; C1 += w * d.y; C2 += w * d.z;
-      N0 += w * cc.y; N1 += w * cc.z; N2 += w * cc.w;
-      if (med < 0 && Tn <= tmed) {
-        med = b0 + j;
-        depth = b.z + b.w * dx + cc.x * dy;
+    for (int c0 = 0; c0 < nb; c0 += 32) {
+      if (__all_sync(kFull, done)) break;
+      const int jl = c0 + lane;
+      unsigned m = __ballot_sync(kFull, jl < nb && (s_m[jl] & wbit));
+      while (m) {
+        const int j = c0 + __ffs(m) - 1;
+        m &= m - 1;
+        if (done) continue;
+        ++evals;
+        const float4 a = s_a[j], b = s_b[j];
+        const float dx = a.x - fpx, dy = a.y - fpy;
+        const float sig = quad(a.z, a.w, b.x, dx, dy);
+        const float al = fminf(amax, b.y * __expf(-sig));
+        if (al < amin) continue;
+        const float Tn = T * (1.f - al);
+        if (Tn < tmin) { done = true; continue; }
+        const float w = al * T;
+        const float4 cc = s_c[j], d = s_d[j];
+        C0 += w * d.x; C1 += w * d.y; C2 += w * d.z;
+        N0 += w * cc.y; N1 += w * cc.z; N2 += w * cc.w;
+        if (med < 0 && Tn <= tmed) {
+          med = b0 + j;
+          depth = b.z + b.w * dx + cc.x * dy;
+        }
+        last = b0 + j;
+        T = Tn;
       }
-      last = b0 + j;
-      T = Tn;
     }
   }
   count_evals(evals, &at<Header>(ws, L.hdr)->n_evals_fwd);
@@ -166,8 +243,9 @@ __device__ inline float warp_reduce_scatter16(float (&v)[16]) {
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_map_grads g) {
+  constexpr int NW = BLOCK / 32;
   __shared__ float4 s_a[BLOCK], s_b[BLOCK], s_c[BLOCK], s_d[BLOCK];
-  __shared__ uint32_t s_e[BLOCK];
+  __shared__ uint32_t s_e[BLOCK], s_m[BLOCK];
   __shared__ int s_max;
   const Header* hdr = at<Header>(ws, L.hdr);
   if (hdr->status == GS_ERR_CAPACITY) return;
@@ -180,6 +258,8 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
   const float amin = fd->alpha_min, amax = fd->alpha_max;
   const float fpx = c.px + 0.5f, fpy = c.py + 0.5f;
   const int lane = threadIdx.x & 31;
+  const uint32_t wbit = 1u << (threadIdx.x >> 5);
+  const int sub_per_row = fd->tile_w / kSubW;
 
   float Tf = 1.f;
   int last = -1, med = -1;
@@ -202,7 +282,8 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
   }
   if (threadIdx.x == 0) s_max = -1;
   __syncthreads();
-  if (last >= 0) atomicMax(&s_max, last);
+  const int wmax = __reduce_max_sync(kFull, last);
+  if (lane == 0 && wmax >= 0) atomicMax(&s_max, wmax);
   __syncthreads();
   const int end = s_max + 1;
 
@@ -216,71 +297,81 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     if (i >= b0) {
       const uint32_t e = pval[i];
       const float4* r = rec + 4 * (int64_t)e;
+      const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3];
       s_e[threadIdx.x] = e;
-      s_a[threadIdx.x] = r[0];
-      s_b[threadIdx.x] = r[1];
-      s_c[threadIdx.x] = r[2];
-      s_d[threadIdx.x] = r[3];
+      s_a[threadIdx.x] = r0;
+      s_b[threadIdx.x] = r1;
+      s_c[threadIdx.x] = r2;
+      s_d[threadIdx.x] = r3;
+      s_m[threadIdx.x] = warp_mask<NW>(r0, r1, r3, c.x0, c.y0, sub_per_row);
     }
     __syncthreads();
     const int n = b1 - b0;
-    for (int j = 0; j < n; ++j) {
-      const int idx = b1 - 1 - j;
-      float gr[16];
+    // entries after the warp's last contributor need no visit
+    const int jmin = max(0, b1 - 1 - wmax);
+    for (int c0 = jmin & ~31; c0 < n; c0 += 32) {
+      const int jl = c0 + lane;
+      unsigned m = __ballot_sync(kFull, jl >= jmin && jl < n && (s_m[jl] & wbit));
+      while (m) {
+        const int j = c0 + __ffs(m) - 1;
+        m &= m - 1;
+        const int idx = b1 - 1 - j;
+        float gr[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) gr[k] = 0.f;
-      bool contrib = false;
-      if (idx <= last) {
-        ++evals;
-        const float4 a = s_a[j], b = s_b[j];
-        const float dx = a.x - fpx, dy = a.y - fpy;
-        const float sig = 0.5f * (a.z * dx * dx + b.x * dy * dy) + a.w * dx * dy;
-        const float G = __expf(-sig);
-        const float raw = b.y * G;
-        const float al = fminf(amax, raw);
-        if (sig >= 0.f && al >= amin) {
-          contrib = true;
-          const float4 cc = s_c[j], d = s_d[j];
-          const float ia = 1.f / (1.f - al);
-          T *= ia;                         // transmittance in front of this splat
-          const float w = al * T;
-          gr[R_R] = w * dC[0]; gr[R_G] = w * dC[1]; gr[R_B] = w * dC[2];
-          gr[R_N0] = w * dN[0]; gr[R_N1] = w * dN[1]; gr[R_N2] = w * dN[2];
-          float dal = T * ((d.x - Sc[0]) * dC[0] + (d.y - Sc[1]) * dC[1] + (d.z - Sc[2]) * dC[2] +
-                           (cc.y - Sn[0]) * dN[0] + (cc.z - Sn[1]) * dN[1] + (cc.w - Sn[2]) * dN[2]) +
-                      dA * Tf * ia;
-          Sc[0] = al * d.x + (1.f - al) * Sc[0];
-          Sc[1] = al * d.y + (1.f - al) * Sc[1];
-          Sc[2] = al * d.z + (1.f - al) * Sc[2];
-          Sn[0] = al * cc.y + (1.f - al) * Sn[0];
-          Sn[1] = al * cc.z + (1.f - al) * Sn[1];
-          Sn[2] = al * cc.w + (1.f - al) * Sn[2];
-          float gu = 0.f, gv = 0.f;
-          if (idx == med) {            // d = z_c + p . Delta (Eq. 4)
-            gr[R_Z] = dD;
-            gr[R_P0] = dD * dx;
-            gr[R_P1] = dD * dy;
-            gu += dD * b.w;
-            gv += dD * cc.x;
+        for (int k = 0; k < 16; ++k) gr[k] = 0.f;
+        bool contrib = false;
+        if (idx <= last) {
+          ++evals;
+          const float4 a = s_a[j], b = s_b[j];
+          const float dx = a.x - fpx, dy = a.y - fpy;
+          const float sig = quad(a.z, a.w, b.x, dx, dy);
+          const float G = __expf(-sig);
+          const float raw = b.y * G;
+          const float al = fminf(amax, raw);
+          if (al >= amin) {
+            contrib = true;
+            const float4 cc = s_c[j], d = s_d[j];
+            const float ia = 1.f / (1.f - al);
+            T *= ia;                         // transmittance in front of this splat
+            const float w = al * T;
+            gr[R_R] = w * dC[0]; gr[R_G] = w * dC[1]; gr[R_B] = w * dC[2];
+            gr[R_N0] = w * dN[0]; gr[R_N1] = w * dN[1]; gr[R_N2] = w * dN[2];
+            const float dal = T * ((d.x - Sc[0]) * dC[0] + (d.y - Sc[1]) * dC[1] + (d.z - Sc[2]) * dC[2] +
+                                   (cc.y - Sn[0]) * dN[0] + (cc.z - Sn[1]) * dN[1] + (cc.w - Sn[2]) * dN[2]) +
+                              dA * Tf * ia;
+            Sc[0] = al * d.x + (1.f - al) * Sc[0];
+            Sc[1] = al * d.y + (1.f - al) * Sc[1];
+            Sc[2] = al * d.z + (1.f - al) * Sc[2];
+            Sn[0] = al * cc.y + (1.f - al) * Sn[0];
+            Sn[1] = al * cc.z + (1.f - al) * Sn[1];
+            Sn[2] = al * cc.w + (1.f - al) * Sn[2];
+            float gu = 0.f, gv = 0.f;
+            if (idx == med) {            // d = z_c + p . Delta (Eq. 4)
+              gr[R_Z] = dD;
+              gr[R_P0] = dD * dx;
+              gr[R_P1] = dD * dy;
+              gu += dD * b.w;
+              gv += dD * cc.x;
+            }
+            if (raw <= amax) {
+              gr[R_O] = dal * G;
+              const float gs = -dal * al;
+              gr[R_CA] = 0.5f * gs * dx * dx;
+              gr[R_CB] = gs * dx * dy;
+              gr[R_CC] = 0.5f * gs * dy * dy;
+              gu += gs * (a.z * dx + a.w * dy);
+              gv += gs * (a.w * dx + b.x * dy);
+            }
+            gr[R_U] = gu;
+            gr[R_V] = gv;
           }
-          if (raw <= amax) {
-            gr[R_O] = dal * G;
-            const float gs = -dal * al;
-            gr[R_CA] = 0.5f * gs * dx * dx;
-            gr[R_CB] = gs * dx * dy;
-            gr[R_CC] = 0.5f * gs * dy * dy;
-            gu += gs * (a.z * dx + a.w * dy);
-            gv += gs * (a.w * dx + b.x * dy);
-          }
-          gr[R_U] = gu;
-          gr[R_V] = gv;
         }
-      }
-      if (__any_sync(kFull, contrib)) {
-        const float s = warp_reduce_scatter16(gr);
-        const int slot = lane >> 1;
-        if ((lane & 1) == 0 && slot < 15 && s != 0.f)
-          atomicAdd(grad + (int64_t)s_e[j] * kRecFloats + slot, s);
+        if (__any_sync(kFull, contrib)) {
+          const float s = warp_reduce_scatter16(gr);
+          const int slot = lane >> 1;
+          if ((lane & 1) == 0 && slot < 15 && s != 0.f)
+            atomicAdd(grad + (int64_t)s_e[j] * kRecFloats + slot, s);
+        }
       }
     }
   }

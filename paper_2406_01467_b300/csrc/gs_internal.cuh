@@ -58,9 +58,10 @@ struct FrameDev {
   int64_t entry_off[GS_MAX_VIEWS + 1];  // entries of view v: [entry_off[v], entry_off[v+1])
   int64_t pix_off[GS_MAX_VIEWS + 1];    // pixels of view v in the concatenated maps
   int32_t tile_off[GS_MAX_VIEWS + 1];   // global tile ids of view v
+  int32_t chunk_off[GS_MAX_VIEWS + 1];  // per-Gaussian kernels: 128-entry chunks before view v
   int32_t n_views, n_scenes;
   int64_t n_entries, n_pixels, pair_capacity;
-  int32_t n_tiles;
+  int32_t n_tiles, n_chunks;
   int32_t tile_w, tile_h, tile_shift_x, tile_shift_y;
   float lowpass, alpha_min, alpha_max, T_min, median_T;
   float ext_c;        // float32(2 ln(1/alpha_min))

@@ -44,3 +44,12 @@ def compare_maps(gpu, ref, margin, tol_abs=TOL_ABS, tol_rel=TOL_DEPTH_REL):
     bad = ok & ((ec > tol_abs) | (ea > tol_abs) | (en > tol_abs) | (ed > tol_rel))
     rep["n_bad"] = int(bad.sum())
     return bad, rep
+
+
+def _same_ranges(got, ref):
+    """Tile ranges agree: identical for non-empty tiles, empty where the oracle's are."""
+    got = np.asarray(got, np.int64)
+    ref = np.asarray(ref, np.int64)
+    full = ref[:, 1] > ref[:, 0]
+    np.testing.assert_array_equal(got[full], ref[full])
+    assert (got[~full, 1] <= got[~full, 0]).all()

@@ -59,6 +59,7 @@ def test_workspace_size_grows_with_inputs(lib):
 @pytest.mark.parametrize("mut, msg", [
     (lambda f: setattr(f.params, "tile_w", 12), "tile"),
     (lambda f: setattr(f.params, "tile_w", 64), "tile"),
+    (lambda f: (setattr(f.params, "tile_w", 64), setattr(f.params, "tile_h", 2)), "tile"),
     (lambda f: setattr(f.params, "alpha_min", 0.0), "alpha_min"),
     (lambda f: setattr(f.params, "alpha_max", 1.0), "alpha_max"),
     (lambda f: setattr(f.params, "median_T", 1.0), "median_T"),

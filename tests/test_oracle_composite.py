@@ -112,7 +112,7 @@ def _literal_composite(scene, cam, prm, pre, dec):
             a, b, c = pre["conic"][g]
             sig = 0.5 * (a * du * du + c * dv * dv) + b * du * dv
             alpha = min(prm.alpha_max, pre["opacity"][g] * math.exp(-sig))
-            if sig < 0 or alpha < prm.alpha_min:
+            if alpha < prm.alpha_min:
                 continue
             Tn = T * (1 - alpha)
             if Tn < prm.T_min:
