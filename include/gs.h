@@ -180,9 +180,9 @@ gs_status gs_preprocess_bwd(const gs_frame* frame, const gs_scene_grads* grads, 
 
 /* Intermediate results for tests and tools, copied to caller device buffers on
  * `stream`; any pointer may be NULL.  rec: [n_entries][16] FP32 per-entry
- * records (u, v, conic a b c, opacity, z, p0 | p1, n0 n1 n2, r g b, spare);
- * (the spare slot holds ln(o / alpha_min) plus a margin: the sigma beyond which a
- * splat cannot reach alpha_min); rect: [n_entries][4] int32 pixel rectangle (i0, i1, j0, j1), (0,-1,0,-1)
+ * records (u, v, conic a b c, opacity, sigma cut, z, p0 p1, n0 n1 n2, r g b);
+ * (the sigma cut is ln(o / alpha_min) plus a margin: beyond it a splat cannot
+ * reach alpha_min); rect: [n_entries][4] int32 pixel rectangle (i0, i1, j0, j1), (0,-1,0,-1)
  * when culled; pair_tile/pair_entry: [pair_capacity] int32 sorted pairs;
  * ranges: [total tiles][2] int32.  grad2d: [n_entries][16] FP32 dL/d(record),
  * valid after gs_render_bwd. */

@@ -10,14 +10,12 @@
 //   (the median depth of Sec. 1), else of the last contributor;
 //   alpha map = 1 - T_final.
 //
-// Each warp owns an 8x4 block of the tile's pixels.  When a batch of records is
-// staged, the thread that loads a record also finds which warps' blocks the
-// splat can reach: the minimum of sigma over the block's rectangle of pixel
-// centres (exact, over its four edges) against sigma_cut = ln(o / alpha_min)
-// with a small safety margin.  A warp walks only the records whose bit it owns,
-// so a splat it skips is one every one of its pixels would have skipped by the
-// alpha test: the maps are the same as without the culling.  The block leaves
-// the loop as soon as every pixel of the tile is done.
+// Each warp owns an 8x4 block of the tile's pixels and walks the tile's list on
+// its own.  A record is evaluated only if the splat can reach the block: the
+// minimum of sigma over the block's rectangle of pixel centres (exact, over its
+// four edges) is at most sigma_cut = ln(o / alpha_min) plus a small margin.  A
+// splat skipped this way is one every pixel of the block would have skipped by
+// the alpha test, so the maps are the same as without the culling.
 //
 // Backward replays each pixel from its last contributor toward the front,
 // recovering T by division (alpha <= alpha_max < 1) and the colour / normal
@@ -97,30 +95,37 @@ __device__ inline float rect_min_sigma(float u, float v, float a, float b, float
   return best;
 }
 
-// Bit w set: the splat can reach a pixel of warp w's block.
-template <int NWARPS>
-__device__ inline uint32_t warp_mask(const float4& r0, const float4& r1, const float4& r3,
-                                     int x0, int y0, int sub_per_row) {
-  const float u = r0.x, v = r0.y, a = r0.z, b = r0.w, c = r1.x;
-  const float cut = r3.w;
-  const float ia = 1.f / a, ic = 1.f / c;
-  uint32_t m = 0;
-#pragma unroll
-  for (int w = 0; w < NWARPS; ++w) {
-    const float X0 = (float)(x0 + (w % sub_per_row) * kSubW) + 0.5f;
-    const float Y0 = (float)(y0 + (w / sub_per_row) * kSubH) + 0.5f;
-    if (rect_min_sigma(u, v, a, b, c, ia, ic, X0, X0 + (kSubW - 1), Y0, Y0 + (kSubH - 1)) <= cut)
-      m |= 1u << w;
-  }
-  return m;
+// Rectangle of warp w's pixel centres inside the tile starting at (x0, y0).
+struct SubRect {
+  float X0, X1, Y0, Y1;
+};
+
+__device__ inline SubRect sub_rect(int x0, int y0, int sub_per_row) {
+  const int w = threadIdx.x >> 5;
+  SubRect r;
+  r.X0 = (float)(x0 + (w % sub_per_row) * kSubW) + 0.5f;
+  r.Y0 = (float)(y0 + (w / sub_per_row) * kSubH) + 0.5f;
+  r.X1 = r.X0 + (kSubW - 1);
+  r.Y1 = r.Y0 + (kSubH - 1);
+  return r;
 }
 
+// Can the splat (first two record float4s) reach any pixel of the rectangle?
+__device__ inline bool reaches(const float4& f0, const float4& f1, const SubRect& R) {
+  const float ia = __fdividef(1.f, f0.z), ic = __fdividef(1.f, f1.x);
+  return rect_min_sigma(f0.x, f0.y, f0.z, f0.w, f1.x, ia, ic, R.X0, R.X1, R.Y0, R.Y1) <= f1.z;
+}
+
+// Each warp walks its tile's list on its own, 32 records at a time: every lane
+// loads one record's first half and tests it against the warp's rectangle; the
+// records that pass are staged whole in the warp's shared slots and evaluated
+// by all 32 lanes in list order.  No block-wide barrier: a warp leaves as soon
+// as its own pixels are done.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_maps maps) {
   constexpr int NW = BLOCK / 32;
-  __shared__ float4 s_a[BLOCK], s_b[BLOCK], s_c[BLOCK], s_d[BLOCK];
-  __shared__ uint32_t s_m[BLOCK];
+  __shared__ float4 s_rec[NW][32][4];
   const Header* hdr = at<Header>(ws, L.hdr);
   if (hdr->status == GS_ERR_CAPACITY) return;
   const int tile = blockIdx.x;
@@ -131,63 +136,62 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
   const float amin = fd->alpha_min, amax = fd->alpha_max, tmin = fd->T_min, tmed = fd->median_T;
   const float fpx = c.px + 0.5f, fpy = c.py + 0.5f;
   const int lane = threadIdx.x & 31;
-  const uint32_t wbit = 1u << (threadIdx.x >> 5);
-  const int sub_per_row = fd->tile_w / kSubW;
+  const SubRect R = sub_rect(c.x0, c.y0, fd->tile_w / kSubW);
+  float4 (*my)[4] = s_rec[threadIdx.x >> 5];
 
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, depth = 0.f;
   int last = -1, med = -1;
   bool done = !c.inside;
   uint32_t evals = 0;
-  for (int b0 = range.x; b0 < range.y; b0 += BLOCK) {
-    if (__syncthreads_count(done) == BLOCK) break;
-    const int i = b0 + threadIdx.x;
+  for (int c0 = range.x; c0 < range.y; c0 += 32) {
+    if (__all_sync(kFull, done)) break;
+    const int i = c0 + lane;
+    bool rel = false;
     if (i < range.y) {
       const float4* r = rec + 4 * (int64_t)pval[i];
-      const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3];
-      s_a[threadIdx.x] = r0;
-      s_b[threadIdx.x] = r1;
-      s_c[threadIdx.x] = r2;
-      s_d[threadIdx.x] = r3;
-      s_m[threadIdx.x] = warp_mask<NW>(r0, r1, r3, c.x0, c.y0, sub_per_row);
-    }
-    __syncthreads();
-    const int nb = min(BLOCK, range.y - b0);
-    for (int c0 = 0; c0 < nb; c0 += 32) {
-      if (__all_sync(kFull, done)) break;
-      const int jl = c0 + lane;
-      unsigned m = __ballot_sync(kFull, jl < nb && (s_m[jl] & wbit));
-      while (m) {
-        const int j = c0 + __ffs(m) - 1;
-        m &= m - 1;
-        if (done) continue;
-        ++evals;
-        const float4 a = s_a[j], b = s_b[j];
-        const float dx = a.x - fpx, dy = a.y - fpy;
-        const float sig = quad(a.z, a.w, b.x, dx, dy);
-        const float al = fminf(amax, b.y * __expf(-sig));
-        if (al < amin) continue;
-        const float Tn = T * (1.f - al);
-        if (Tn < tmin) { done = true; continue; }
-        const float w = al * T;
-        const float4 cc = s_c[j], d = s_d[j];
-        C0 += w * d.x; C1 += w * d.y; C2 += w * d.z;
-        N0 += w * cc.y; N1 += w * cc.z; N2 += w * cc.w;
-        if (med < 0 && Tn <= tmed) {
-          med = b0 + j;
-          depth = b.z + b.w * dx + cc.x * dy;
-        }
-        last = b0 + j;
-        T = Tn;
+      const float4 f0 = __ldg(r), f1 = __ldg(r + 1);
+      rel = reaches(f0, f1, R);
+      if (rel) {
+        my[lane][0] = f0;
+        my[lane][1] = f1;
+        my[lane][2] = __ldg(r + 2);
+        my[lane][3] = __ldg(r + 3);
       }
     }
+    unsigned m = __ballot_sync(kFull, rel);
+    __syncwarp();
+    while (m) {
+      const int j = __ffs(m) - 1;
+      m &= m - 1;
+      if (done) continue;
+      ++evals;
+      const float4 a = my[j][0], b = my[j][1];
+      const float dx = a.x - fpx, dy = a.y - fpy;
+      const float sig = quad(a.z, a.w, b.x, dx, dy);
+      const float al = fminf(amax, b.y * __expf(-sig));
+      if (al < amin) continue;
+      const float Tn = T * (1.f - al);
+      if (Tn < tmin) { done = true; continue; }
+      const float w = al * T;
+      const float4 e2 = my[j][2], e3 = my[j][3];
+      C0 += w * e3.y; C1 += w * e3.z; C2 += w * e3.w;
+      N0 += w * e2.z; N1 += w * e2.w; N2 += w * e3.x;
+      if (med < 0 && Tn <= tmed) {
+        med = c0 + j;
+        depth = b.w + e2.x * dx + e2.y * dy;   // Eq. 4
+      }
+      last = c0 + j;
+      T = Tn;
+    }
+    __syncwarp();
   }
   count_evals(evals, &at<Header>(ws, L.hdr)->n_evals_fwd);
   if (!c.inside) return;
   if (med < 0 && last >= 0) {   // median never reached: depth of the last contributor
     med = last;
     const float4* r = rec + 4 * (int64_t)pval[last];
-    const float4 a = r[0], b = r[1], cc = r[2];
-    depth = b.z + b.w * (a.x - fpx) + cc.x * (a.y - fpy);
+    const float4 a = r[0], b = r[1], e2 = r[2];
+    depth = b.w + e2.x * (a.x - fpx) + e2.y * (a.y - fpy);
   }
   const int64_t HW = (int64_t)c.W * c.H;
   const int64_t p = c.pix_local;
@@ -244,9 +248,8 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_map_grads g) {
   constexpr int NW = BLOCK / 32;
-  __shared__ float4 s_a[BLOCK], s_b[BLOCK], s_c[BLOCK], s_d[BLOCK];
-  __shared__ uint32_t s_e[BLOCK], s_m[BLOCK];
-  __shared__ int s_max;
+  __shared__ float4 s_rec[NW][32][4];
+  __shared__ uint32_t s_ent[NW][32];
   const Header* hdr = at<Header>(ws, L.hdr);
   if (hdr->status == GS_ERR_CAPACITY) return;
   const int tile = blockIdx.x;
@@ -258,8 +261,9 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
   const float amin = fd->alpha_min, amax = fd->alpha_max;
   const float fpx = c.px + 0.5f, fpy = c.py + 0.5f;
   const int lane = threadIdx.x & 31;
-  const uint32_t wbit = 1u << (threadIdx.x >> 5);
-  const int sub_per_row = fd->tile_w / kSubW;
+  const SubRect R = sub_rect(c.x0, c.y0, fd->tile_w / kSubW);
+  float4 (*my)[4] = s_rec[threadIdx.x >> 5];
+  uint32_t* my_e = s_ent[threadIdx.x >> 5];
 
   float Tf = 1.f;
   int last = -1, med = -1;
@@ -280,100 +284,91 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     if (g.dalpha) dA = g.dalpha[c.pix];
     if (g.ddepth) dD = g.ddepth[c.pix];
   }
-  if (threadIdx.x == 0) s_max = -1;
-  __syncthreads();
   const int wmax = __reduce_max_sync(kFull, last);
-  if (lane == 0 && wmax >= 0) atomicMax(&s_max, wmax);
-  __syncthreads();
-  const int end = s_max + 1;
 
   float T = Tf;
   float Sc[3] = {0.f, 0.f, 0.f}, Sn[3] = {0.f, 0.f, 0.f};
   uint32_t evals = 0;
-  for (int b1 = end; b1 > range.x; b1 -= BLOCK) {
-    const int b0 = max(range.x, b1 - BLOCK);
-    __syncthreads();
-    const int i = b1 - 1 - (int)threadIdx.x;
-    if (i >= b0) {
+  for (int c1 = wmax + 1; c1 > range.x; c1 -= 32) {
+    const int i = c1 - 1 - lane;          // lane 0 holds the farthest record of the chunk
+    bool rel = false;
+    if (i >= range.x) {
       const uint32_t e = pval[i];
       const float4* r = rec + 4 * (int64_t)e;
-      const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3];
-      s_e[threadIdx.x] = e;
-      s_a[threadIdx.x] = r0;
-      s_b[threadIdx.x] = r1;
-      s_c[threadIdx.x] = r2;
-      s_d[threadIdx.x] = r3;
-      s_m[threadIdx.x] = warp_mask<NW>(r0, r1, r3, c.x0, c.y0, sub_per_row);
-    }
-    __syncthreads();
-    const int n = b1 - b0;
-    // entries after the warp's last contributor need no visit
-    const int jmin = max(0, b1 - 1 - wmax);
-    for (int c0 = jmin & ~31; c0 < n; c0 += 32) {
-      const int jl = c0 + lane;
-      unsigned m = __ballot_sync(kFull, jl >= jmin && jl < n && (s_m[jl] & wbit));
-      while (m) {
-        const int j = c0 + __ffs(m) - 1;
-        m &= m - 1;
-        const int idx = b1 - 1 - j;
-        float gr[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) gr[k] = 0.f;
-        bool contrib = false;
-        if (idx <= last) {
-          ++evals;
-          const float4 a = s_a[j], b = s_b[j];
-          const float dx = a.x - fpx, dy = a.y - fpy;
-          const float sig = quad(a.z, a.w, b.x, dx, dy);
-          const float G = __expf(-sig);
-          const float raw = b.y * G;
-          const float al = fminf(amax, raw);
-          if (al >= amin) {
-            contrib = true;
-            const float4 cc = s_c[j], d = s_d[j];
-            const float ia = 1.f / (1.f - al);
-            T *= ia;                         // transmittance in front of this splat
-            const float w = al * T;
-            gr[R_R] = w * dC[0]; gr[R_G] = w * dC[1]; gr[R_B] = w * dC[2];
-            gr[R_N0] = w * dN[0]; gr[R_N1] = w * dN[1]; gr[R_N2] = w * dN[2];
-            const float dal = T * ((d.x - Sc[0]) * dC[0] + (d.y - Sc[1]) * dC[1] + (d.z - Sc[2]) * dC[2] +
-                                   (cc.y - Sn[0]) * dN[0] + (cc.z - Sn[1]) * dN[1] + (cc.w - Sn[2]) * dN[2]) +
-                              dA * Tf * ia;
-            Sc[0] = al * d.x + (1.f - al) * Sc[0];
-            Sc[1] = al * d.y + (1.f - al) * Sc[1];
-            Sc[2] = al * d.z + (1.f - al) * Sc[2];
-            Sn[0] = al * cc.y + (1.f - al) * Sn[0];
-            Sn[1] = al * cc.z + (1.f - al) * Sn[1];
-            Sn[2] = al * cc.w + (1.f - al) * Sn[2];
-            float gu = 0.f, gv = 0.f;
-            if (idx == med) {            // d = z_c + p . Delta (Eq. 4)
-              gr[R_Z] = dD;
-              gr[R_P0] = dD * dx;
-              gr[R_P1] = dD * dy;
-              gu += dD * b.w;
-              gv += dD * cc.x;
-            }
-            if (raw <= amax) {
-              gr[R_O] = dal * G;
-              const float gs = -dal * al;
-              gr[R_CA] = 0.5f * gs * dx * dx;
-              gr[R_CB] = gs * dx * dy;
-              gr[R_CC] = 0.5f * gs * dy * dy;
-              gu += gs * (a.z * dx + a.w * dy);
-              gv += gs * (a.w * dx + b.x * dy);
-            }
-            gr[R_U] = gu;
-            gr[R_V] = gv;
-          }
-        }
-        if (__any_sync(kFull, contrib)) {
-          const float s = warp_reduce_scatter16(gr);
-          const int slot = lane >> 1;
-          if ((lane & 1) == 0 && slot < 15 && s != 0.f)
-            atomicAdd(grad + (int64_t)s_e[j] * kRecFloats + slot, s);
-        }
+      const float4 f0 = __ldg(r), f1 = __ldg(r + 1);
+      rel = reaches(f0, f1, R);
+      if (rel) {
+        my[lane][0] = f0;
+        my[lane][1] = f1;
+        my[lane][2] = __ldg(r + 2);
+        my[lane][3] = __ldg(r + 3);
+        my_e[lane] = e;
       }
     }
+    unsigned m = __ballot_sync(kFull, rel);
+    __syncwarp();
+    while (m) {
+      const int j = __ffs(m) - 1;
+      m &= m - 1;
+      const int idx = c1 - 1 - j;
+      float gr[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) gr[k] = 0.f;
+      bool contrib = false;
+      if (idx <= last) {
+        ++evals;
+        const float4 a = my[j][0], b = my[j][1];
+        const float dx = a.x - fpx, dy = a.y - fpy;
+        const float sig = quad(a.z, a.w, b.x, dx, dy);
+        const float G = __expf(-sig);
+        const float raw = b.y * G;
+        const float al = fminf(amax, raw);
+        if (al >= amin) {
+          contrib = true;
+          const float4 e2 = my[j][2], e3 = my[j][3];
+          const float rgb[3] = {e3.y, e3.z, e3.w}, nrm[3] = {e2.z, e2.w, e3.x};
+          const float ia = 1.f / (1.f - al);
+          T *= ia;                         // transmittance in front of this splat
+          const float w = al * T;
+          gr[R_R] = w * dC[0]; gr[R_G] = w * dC[1]; gr[R_B] = w * dC[2];
+          gr[R_N0] = w * dN[0]; gr[R_N1] = w * dN[1]; gr[R_N2] = w * dN[2];
+          const float dal = T * ((rgb[0] - Sc[0]) * dC[0] + (rgb[1] - Sc[1]) * dC[1] + (rgb[2] - Sc[2]) * dC[2] +
+                                 (nrm[0] - Sn[0]) * dN[0] + (nrm[1] - Sn[1]) * dN[1] + (nrm[2] - Sn[2]) * dN[2]) +
+                            dA * Tf * ia;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            Sc[k] = al * rgb[k] + (1.f - al) * Sc[k];
+            Sn[k] = al * nrm[k] + (1.f - al) * Sn[k];
+          }
+          float gu = 0.f, gv = 0.f;
+          if (idx == med) {            // d = z_c + p . Delta (Eq. 4)
+            gr[R_Z] = dD;
+            gr[R_P0] = dD * dx;
+            gr[R_P1] = dD * dy;
+            gu += dD * e2.x;
+            gv += dD * e2.y;
+          }
+          if (raw <= amax) {
+            gr[R_O] = dal * G;
+            const float gs = -dal * al;
+            gr[R_CA] = 0.5f * gs * dx * dx;
+            gr[R_CB] = gs * dx * dy;
+            gr[R_CC] = 0.5f * gs * dy * dy;
+            gu += gs * (a.z * dx + a.w * dy);
+            gv += gs * (a.w * dx + b.x * dy);
+          }
+          gr[R_U] = gu;
+          gr[R_V] = gv;
+        }
+      }
+      if (__any_sync(kFull, contrib)) {
+        const float s = warp_reduce_scatter16(gr);
+        const int slot = lane >> 1;
+        if ((lane & 1) == 0 && slot != R_CUT && s != 0.f)
+          atomicAdd(grad + (int64_t)my_e[j] * kRecFloats + slot, s);
+      }
+    }
+    __syncwarp();
   }
   count_evals(evals, &at<Header>(ws, L.hdr)->n_evals_bwd);
 }

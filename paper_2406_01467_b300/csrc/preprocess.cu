@@ -404,13 +404,13 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
     if (!finite) ++nonfinite;
     if (valid) {
       float4* r = rec + 4 * e;
-      r[0] = make_float4(u, v, conic[0], conic[1]);
-      r[1] = make_float4(conic[2], o, z, pp[0]);
-      r[2] = make_float4(pp[1], nn[0], nn[1], nn[2]);
       // sigma beyond which alpha < alpha_min (with a margin far above FP32 error):
       // lets the compositing skip a splat for a whole block of pixels
       const float cut = logf(o / amin) * 1.0001f + 1e-4f;
-      r[3] = make_float4(rgb[0], rgb[1], rgb[2], cut);
+      r[0] = make_float4(u, v, conic[0], conic[1]);
+      r[1] = make_float4(conic[2], o, cut, z);
+      r[2] = make_float4(pp[0], pp[1], nn[0], nn[1]);
+      r[3] = make_float4(nn[2], rgb[0], rgb[1], rgb[2]);
       rect[e] = make_short4((short)i0, (short)i1, (short)j0, (short)j1);
       key[e] = __float_as_uint(z);
       touched[e] = (uint32_t)(((i1 >> sx) - (i0 >> sx) + 1) * ((j1 >> sy) - (j0 >> sy) + 1));
@@ -497,10 +497,10 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
       geo_forward(V, m, s, q, lp, g);
       const float4 ga = g2d[4 * e], gb4 = g2d[4 * e + 1], gc4 = g2d[4 * e + 2], gd4 = g2d[4 * e + 3];
       const float gu = ga.x, gv = ga.y, gca = ga.z, gcb = ga.w;
-      const float gcc = gb4.x, gz = gb4.z, gp0 = gb4.w;
+      const float gcc = gb4.x, gz = gb4.w;
       go = gb4.y;
-      const float gp1 = gc4.x, gn[3] = {gc4.y, gc4.z, gc4.w};
-      const float grgb[3] = {gd4.x, gd4.y, gd4.z};
+      const float gp0 = gc4.x, gp1 = gc4.y, gn[3] = {gc4.z, gc4.w, gd4.x};
+      const float grgb[3] = {gd4.y, gd4.z, gd4.w};
 
       // ---- colour: rgb = max(sum Y_j c_j + 1/2, 0) ----------------------------
       {
