@@ -249,15 +249,19 @@ def run_ours(args, rank, world, device):
     hbm = peaks["hbm_gbs"]
     alu_peak = N_SM * FP32_LANES * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # T lane-ops/s
     OPS_FWD, OPS_BWD = 20, 55
+    gbytes = 4 * (3 + 3 + 4 + 1)          # geometry + opacity of one Gaussian
+    shbytes = pbytes - gbytes             # its SH coefficients
     algo = {
-        # bytes: every parameter read, record + rect + key + count written
-        "preprocess": ("hbm", N * pbytes + nvis * 64 + N * 16),
+        # bytes: geometry + opacity of every Gaussian, SH of the visible ones read;
+        # record of the visible ones and rect + key + count of all written
+        "preprocess": ("hbm", N * gbytes + nvis * shbytes + nvis * 64 + N * 16),
         # bytes: per pair one read and one write per sort pass lower bound (24 B), depth keys
         "bin": ("hbm", P * 24 + nvis * 16 + N * 8),
         "render_fwd": ("alu", ev_f * OPS_FWD),
         "composite_bwd": ("alu", ev_b * OPS_BWD),
-        # bytes: parameters + 2D gradients of visible entries read, all parameter gradients written
-        "preprocess_bwd": ("hbm", nvis * (pbytes + 64) + N * pbytes),
+        # bytes: key of every entry, parameters + 2D gradients of visible entries read,
+        # all parameter gradients written
+        "preprocess_bwd": ("hbm", N * 4 + nvis * (pbytes + 64) + N * pbytes),
     }
     roof = {}
     for k, (bound, work) in algo.items():

@@ -166,7 +166,10 @@ k_compact(const uint32_t* __restrict__ key, int64_t E, const uint32_t* __restric
   }
 }
 
-// Emission of (tile, entry) pairs in depth order.
+// Emission of (tile, entry) pairs in depth order.  Each warp takes its 32
+// entries of a round together: lane l writes pairs l, l+32, ... of the round's
+// concatenated pair list, finding its entry by a binary search over the warp's
+// inclusive scan, so the stores are contiguous and big splats are shared out.
 __global__ void __launch_bounds__(kSortThreads)
 k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
        const unsigned long long* n_vis_ptr, int64_t E, const uint32_t* __restrict__ touched,
@@ -178,11 +181,15 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   if (base >= n) return;
   uint32_t ent[kSortItems], cnt[kSortItems];
-  uint32_t wsum = 0;
+#pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    int64_t i = WarpItems::index(base, r);
-    ent[r] = i < n ? sval[i] : 0u;
-    cnt[r] = i < n ? touched[ent[r]] : 0u;
+    const int64_t i = WarpItems::index(base, r);
+    ent[r] = i < n ? __ldg(sval + i) : 0u;
+  }
+  uint32_t wsum = 0;
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    cnt[r] = WarpItems::index(base, r) < n ? __ldg(touched + ent[r]) : 0u;
     uint32_t x = cnt[r];
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
     wsum += x;
@@ -196,26 +203,47 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
   for (int r = 0; r < kSortItems; ++r) {
     uint32_t x = cnt[r];
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(FULL, x, o);
+      const uint32_t y = __shfl_up_sync(FULL, x, o);
       if (lane >= o) x += y;
     }
-    uint64_t my = off + x - cnt[r];
-    off += __shfl_sync(FULL, x, 31);
-    if (cnt[r] == 0) continue;
+    const uint32_t total = __shfl_sync(FULL, x, 31);
+    // this lane's entry, its first tile and row length, for the others to read
     const uint32_t e = ent[r];
-    const int vi = find_view(fd->entry_off, nv, (int64_t)e);
-    const int tx_n = fd->views[vi].tiles_x;
-    const int toff = fd->tile_off[vi];
-    const short4 rc = rect[e];
-    const int tx0 = rc.x >> sx, tx1 = rc.y >> sx, ty0 = rc.z >> sy, ty1 = rc.w >> sy;
-    for (int ty = ty0; ty <= ty1; ++ty)
-      for (int tx = tx0; tx <= tx1; ++tx) {
-        if (my < (uint64_t)cap) {
-          ptile[my] = (uint32_t)(toff + ty * tx_n + tx);
-          pval[my] = e;
-        }
-        ++my;
+    int tx0 = 0, ty0 = 0, nx = 1, rowlen = 0, toff = 0;
+    if (cnt[r]) {
+      const int vi = find_view(fd->entry_off, nv, (int64_t)e);
+      const short4 rc = rect[e];
+      tx0 = rc.x >> sx;
+      ty0 = rc.z >> sy;
+      nx = (rc.y >> sx) - tx0 + 1;
+      rowlen = fd->views[vi].tiles_x;
+      toff = fd->tile_off[vi];
+    }
+    for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+      const uint32_t p = k0 + lane;
+      // owner: first lane whose inclusive count exceeds p
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t xv = __shfl_sync(FULL, x, lo + step - 1);
+        if (xv <= p) lo += step;
       }
+      const uint32_t xo = __shfl_sync(FULL, x, lo), co = __shfl_sync(FULL, cnt[r], lo);
+      const uint32_t eo = __shfl_sync(FULL, e, lo);
+      const int tx0o = __shfl_sync(FULL, tx0, lo), ty0o = __shfl_sync(FULL, ty0, lo);
+      const int nxo = __shfl_sync(FULL, nx, lo), rlo = __shfl_sync(FULL, rowlen, lo);
+      const int tofo = __shfl_sync(FULL, toff, lo);
+      if (p < total) {
+        const uint32_t local = p - (xo - co);
+        const uint32_t ty = local / (uint32_t)nxo, tx = local - ty * (uint32_t)nxo;
+        const uint64_t dst = off + p;
+        if (dst < (uint64_t)cap) {
+          ptile[dst] = (uint32_t)(tofo + (ty0o + (int)ty) * rlo + tx0o + (int)tx);
+          pval[dst] = eo;
+        }
+      }
+    }
+    off += total;
   }
 }
 
@@ -226,26 +254,31 @@ __global__ void __launch_bounds__(kSortThreads)
 k_radix_hist(const uint32_t* __restrict__ kin, const unsigned long long* count_ptr, int64_t cap,
              int shift, uint32_t* __restrict__ hist, int nb) {
   __shared__ uint32_t s_h[8][kRadix];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&s_h[0][0])[i] = 0;
   __syncthreads();
   const int64_t n = clamp_count(count_ptr, cap);
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   if (base < n) {
+    int d[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {   // all loads in flight before any ranking
+      const int64_t i = WarpItems::index(base, r);
+      d[r] = i < n ? (int)((__ldg(kin + i) >> shift) & (kRadix - 1)) : kRadix;
+    }
+    const unsigned lt = lanemask_lt();
+#pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
-      int64_t i = WarpItems::index(base, r);
-      int d = i < n ? (int)((kin[i] >> shift) & (kRadix - 1)) : kRadix;
-      unsigned peers = __match_any_sync(FULL, d);
-      if (d < kRadix && (peers & lanemask_lt()) == 0) s_h[w][d] += __popc(peers);
+      const unsigned peers = __match_any_sync(FULL, d[r]);
+      if (d[r] < kRadix && (peers & lt) == 0) s_h[w][d[r]] += __popc(peers);
       __syncwarp();
     }
   }
   __syncthreads();
-  const int d = threadIdx.x;
+  const int dg = threadIdx.x;
   uint32_t s = 0;
-  for (int i = 0; i < 8; ++i) s += s_h[i][d];
-  hist[(int64_t)d * nb + blockIdx.x] = s;
-  (void)lane;
+  for (int i = 0; i < 8; ++i) s += s_h[i][dg];
+  hist[(int64_t)dg * nb + blockIdx.x] = s;
 }
 
 // Block d scans hist[d][0..nb) (exclusive, in place) and writes the digit total.
@@ -295,11 +328,15 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
   __syncthreads();
   uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
   const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {   // all loads in flight before any ranking
+    const int64_t i = WarpItems::index(base, r);
+    k[r] = i < n ? __ldg(kin + i) : 0u;
+    v[r] = i < n ? __ldg(vin + i) : 0u;
+  }
+#pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    int64_t i = WarpItems::index(base, r);
-    const bool ok = i < n;
-    k[r] = ok ? kin[i] : 0u;
-    v[r] = ok ? vin[i] : 0u;
+    const bool ok = WarpItems::index(base, r) < n;
     int d = ok ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
     unsigned peers = __match_any_sync(FULL, d);
     uint32_t old = d < kRadix ? s_wcnt[d][w] : 0u;

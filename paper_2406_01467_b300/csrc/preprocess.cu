@@ -182,74 +182,83 @@ __device__ inline Chunk chunk_of(const FrameDev* fd, int b) {
 
 template <typename T> __host__ __device__ constexpr int dtype_code() { return sizeof(T) == 4 ? GS_F32 : GS_BF16; }
 
-// Coalesced copy of a chunk's contiguous parameter block into shared memory,
-// widened to FP32; element i goes to dst[(i / group) * stride + i % group].
-// 16-byte vector loads, four in flight per thread, when the source is aligned.
-template <int GROUP, int STRIDE>
-__device__ inline void put_elem(float* dst, int i, float v, int* bad) {
-  dst[(i / GROUP) * STRIDE + i % GROUP] = v;
-  if (bad && !(fabsf(v) <= 3.402823466e38f)) bad[i / GROUP] = 1;   // nan or inf
+// Element i of a shared-memory array of T, widened to FP32.
+template <typename T> __device__ inline float lds(const T* p, int i);
+template <> __device__ inline float lds<float>(const float* p, int i) { return p[i]; }
+template <> __device__ inline float lds<__nv_bfloat16>(const __nv_bfloat16* p, int i) {
+  return __bfloat162float(p[i]);
+}
+// The same through a volatile pointer: the compiler neither caches nor reuses it.
+template <typename T> __device__ inline float lds_volatile(const T* p, int i);
+template <> __device__ inline float lds_volatile<float>(const float* p, int i) {
+  return reinterpret_cast<const volatile float*>(p)[i];
+}
+template <> __device__ inline float lds_volatile<__nv_bfloat16>(const __nv_bfloat16* p, int i) {
+  return __uint_as_float((uint32_t)reinterpret_cast<const volatile unsigned short*>(p)[i] << 16);
 }
 
-template <typename T, int GROUP, int STRIDE>
-__device__ inline void stage(const T* __restrict__ src, int count, float* __restrict__ dst,
-                             int* bad = nullptr) {
-  constexpr int PER = 16 / sizeof(T);   // elements per 16-byte vector
-  int done = 0;
-  if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-    const int nv = count / PER;
-    const uint4* s4 = reinterpret_cast<const uint4*>(src);
-    for (int base = 0; base < nv; base += 4 * (int)blockDim.x) {
-      uint4 r[4];
+// Global loads of one Gaussian's parameters, widened to FP32.
+template <typename T>
+__device__ inline void load_gauss(const SceneDev& S, int64_t g, float m[3], float s[3], float q[4], float& o);
+template <>
+__device__ inline void load_gauss<float>(const SceneDev& S, int64_t g, float m[3], float s[3], float q[4],
+                                         float& o) {
+  const float* mp = static_cast<const float*>(S.means) + 3 * g;
+  const float* sp = static_cast<const float*>(S.scales) + 3 * g;
+  for (int k = 0; k < 3; ++k) { m[k] = __ldg(mp + k); s[k] = __ldg(sp + k); }
+  const float* qp = static_cast<const float*>(S.quats) + 4 * g;
+  if ((reinterpret_cast<uintptr_t>(qp) & 15) == 0) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(qp));
+    q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+  } else {
+    for (int k = 0; k < 4; ++k) q[k] = __ldg(qp + k);
+  }
+  o = __ldg(static_cast<const float*>(S.opacities) + g);
+}
+template <>
+__device__ inline void load_gauss<__nv_bfloat16>(const SceneDev& S, int64_t g, float m[3], float s[3], float q[4],
+                                                 float& o) {
+  const __nv_bfloat16* mp = static_cast<const __nv_bfloat16*>(S.means) + 3 * g;
+  const __nv_bfloat16* sp = static_cast<const __nv_bfloat16*>(S.scales) + 3 * g;
+  const __nv_bfloat16* qp = static_cast<const __nv_bfloat16*>(S.quats) + 4 * g;
+  for (int k = 0; k < 3; ++k) { m[k] = __bfloat162float(mp[k]); s[k] = __bfloat162float(sp[k]); }
+  for (int k = 0; k < 4; ++k) q[k] = __bfloat162float(qp[k]);
+  o = __bfloat162float(static_cast<const __nv_bfloat16*>(S.opacities)[g]);
+}
+
+// A Gaussian's 3K SH coefficients, widened to FP32 (16-byte loads when aligned).
+template <typename T, int K>
+__device__ inline void load_sh(const SceneDev& S, int64_t g, float* c) {
+  const T* p = static_cast<const T*>(S.sh) + 3 * K * g;
+  constexpr int PER = 16 / (int)sizeof(T);
+  if ((3 * K) % PER == 0 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+#pragma unroll
+    for (int f = 0; f < 3 * K / PER; ++f) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + f);
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const int f = base + k * blockDim.x + threadIdx.x;
-        if (f < nv) r[k] = __ldg(s4 + f);
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int f = base + k * blockDim.x + threadIdx.x;
-        if (f >= nv) continue;
-        const uint32_t w[4] = {r[k].x, r[k].y, r[k].z, r[k].w};
         if (sizeof(T) == 4) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) put_elem<GROUP, STRIDE>(dst, PER * f + c, __uint_as_float(w[c]), bad);
+          c[PER * f + k] = __uint_as_float(w[k]);
         } else {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            put_elem<GROUP, STRIDE>(dst, PER * f + 2 * c, __uint_as_float(w[c] << 16), bad);
-            put_elem<GROUP, STRIDE>(dst, PER * f + 2 * c + 1, __uint_as_float(w[c] & 0xFFFF0000u), bad);
-          }
+          c[PER * f + 2 * k] = __uint_as_float(w[k] << 16);
+          c[PER * f + 2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
         }
       }
     }
-    done = nv * PER;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 3 * K; ++j) c[j] = ldf(p, j);
   }
-  for (int i = done + threadIdx.x; i < count; i += blockDim.x) put_elem<GROUP, STRIDE>(dst, i, ldf(src, i), bad);
-}
-
-template <typename T>
-__device__ inline void load_quat(const T* q, int64_t g, float out[4]);
-template <> __device__ inline void load_quat<float>(const float* q, int64_t g, float out[4]) {
-  const float4 v = __ldg(reinterpret_cast<const float4*>(q) + g);
-  out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
-}
-template <> __device__ inline void load_quat<__nv_bfloat16>(const __nv_bfloat16* q, int64_t g, float out[4]) {
-  const uint2 v = __ldg(reinterpret_cast<const uint2*>(q) + g);
-  out[0] = __uint_as_float(v.x << 16); out[1] = __uint_as_float(v.x & 0xFFFF0000u);
-  out[2] = __uint_as_float(v.y << 16); out[3] = __uint_as_float(v.y & 0xFFFF0000u);
 }
 
 // ---------------------------------------------------------------------------
 // Forward
 // ---------------------------------------------------------------------------
 template <typename T, int D>
-__global__ void __launch_bounds__(kPreThreads, 4)
+__global__ void __launch_bounds__(kPreThreads)
 k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
-  constexpr int K = (D + 1) * (D + 1), SHS = 3 * K + 1;
-  __shared__ float s_sh[kPreThreads * SHS];
-  __shared__ float s_m[kPreThreads * 3], s_s[kPreThreads * 3], s_o[kPreThreads];
-  __shared__ int s_bad[kPreThreads];
+  constexpr int K = (D + 1) * (D + 1);
   Header* hdr = at<Header>(ws, L.hdr);
   float4* rec = at<float4>(ws, L.rec);
   short4* rect = at<short4>(ws, L.rect);
@@ -263,28 +272,17 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
     const ViewDev& V = fd->views[ch.view];
     const SceneDev& S = fd->scenes[V.scene];
     if (S.dtype != dtype_code<T>() || S.sh_degree != D) continue;
-    __syncthreads();
-    s_bad[threadIdx.x] = 0;
-    __syncthreads();
-    stage<T, 3, 3>(static_cast<const T*>(S.means) + 3 * ch.g0, 3 * ch.n, s_m, s_bad);
-    stage<T, 3, 3>(static_cast<const T*>(S.scales) + 3 * ch.g0, 3 * ch.n, s_s, s_bad);
-    stage<T, 1, 1>(static_cast<const T*>(S.opacities) + ch.g0, ch.n, s_o, s_bad);
-    stage<T, 3 * K, SHS>(static_cast<const T*>(S.sh) + 3 * K * ch.g0, 3 * K * ch.n, s_sh, s_bad);
-    __syncthreads();
     const int t = threadIdx.x;
     if (t >= ch.n) continue;
-    const int64_t e = ch.e0 + t;
-    float m[3], s[3], q[4];
-    for (int k = 0; k < 3; ++k) { m[k] = s_m[3 * t + k]; s[k] = s_s[3 * t + k]; }
-    load_quat<T>(static_cast<const T*>(S.quats), ch.g0 + t, q);
-    const float o = s_o[t];
-    const float* sh = s_sh + t * SHS;
-
-    // finiteness of every input: staged arrays were checked on load
-    float chk = 0.f;
-    for (int k = 0; k < 4; ++k) chk += q[k] * 0.f;   // inf * 0 and nan * 0 are nan
-    const bool finite = chk == 0.f && s_bad[t] == 0;
-
+    const int64_t e = ch.e0 + t, g = ch.g0 + t;
+    float m[3], s[3], q[4], o;
+    load_gauss<T>(S, g, m, s, q, o);
+    float chk = 0.f;   // inf * 0 and nan * 0 are nan
+    for (int k = 0; k < 3; ++k) chk += m[k] * 0.f + s[k] * 0.f;
+    for (int k = 0; k < 4; ++k) chk += q[k] * 0.f;
+    chk += o * 0.f;
+    const bool finite = chk == 0.f;
+    if (!finite) ++nonfinite;
     // ---- exactly rounded decision chain ----------------------------------
     float xc[3];
     for (int i = 0; i < 3; ++i)
@@ -359,6 +357,13 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
     float conic[3] = {0.f, 0.f, 0.f}, pp[2] = {0.f, 0.f}, nn[3] = {0.f, 0.f, 0.f};
     float rgb[3] = {0.f, 0.f, 0.f};
     if (valid) {
+      // SH coefficients are read only for entries that survive the culling
+      float c[3 * K];
+      load_sh<T, K>(S, g, c);
+      float shchk = 0.f;
+#pragma unroll
+      for (int j = 0; j < 3 * K; ++j) shchk += c[j] * 0.f;
+      if (shchk != 0.f) { valid = false; ++nonfinite; }
       const float tc = sqrtf(xc[0] * xc[0] + xc[1] * xc[1] + xc[2] * xc[2]);
       const float it = 1.f / tc;
       const float J2[3] = {xc[0] * it, xc[1] * it, xc[2] * it};   // third row of J: d|x|/dx
@@ -387,21 +392,20 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
       const float mv2 = -(q0 * j02 + q1 * j12 + J2[2]);
       const float im = rsqrtf(mv0 * mv0 + mv1 * mv1 + mv2 * mv2);
       nn[0] = mv0 * im; nn[1] = mv1 * im; nn[2] = mv2 * im;
-      valid = (det > 0.f) && isfinite(conic[0]) && isfinite(conic[1]) && isfinite(conic[2]) &&
+      valid = valid && (det > 0.f) && isfinite(conic[0]) && isfinite(conic[1]) && isfinite(conic[2]) &&
               isfinite(pp[0]) && isfinite(pp[1]) && isfinite(nn[0]) && isfinite(nn[1]) && isfinite(nn[2]);
       float d[3] = {m[0] - V.campos[0], m[1] - V.campos[1], m[2] - V.campos[2]};
       float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
       float Y[16];
       sh_basis(d[0] * il, d[1] * il, d[2] * il, Y);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+      for (int ch3 = 0; ch3 < 3; ++ch3) {
         float acc = 0.5f;
 #pragma unroll
-        for (int j = 0; j < K; ++j) acc += Y[j] * sh[3 * j + c];
-        rgb[c] = fmaxf(acc, 0.f);
+        for (int j = 0; j < K; ++j) acc += Y[j] * c[3 * j + ch3];
+        rgb[ch3] = fmaxf(acc, 0.f);
       }
     }
-    if (!finite) ++nonfinite;
     if (valid) {
       float4* r = rec + 4 * e;
       // sigma beyond which alpha < alpha_min (with a margin far above FP32 error):
@@ -430,43 +434,10 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
 // ---------------------------------------------------------------------------
 // Backward: d(record) -> d(means, scales, quats, opacities, sh)
 // ---------------------------------------------------------------------------
-// Writes a staged gradient block: plain stores if the scene has one view, else
-// atomic adds (the buffers were zeroed first).  Stores go out as 16-byte
-// vectors when the destination is aligned.
-template <int GROUP, int STRIDE>
-__device__ inline float get_elem(const float* src, int i) {
-  return src[(i / GROUP) * STRIDE + i % GROUP];
-}
-
-template <int GROUP, int STRIDE>
-__device__ inline void unstage(const float* __restrict__ src, int count, float* __restrict__ dst, bool store) {
-  if (!dst) return;
-  if (!store) {
-    for (int i = threadIdx.x; i < count; i += blockDim.x) {
-      const float v = get_elem<GROUP, STRIDE>(src, i);
-      if (v != 0.f) atomicAdd(dst + i, v);
-    }
-    return;
-  }
-  int done = 0;
-  if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-    const int nv = count / 4;
-    float4* d4 = reinterpret_cast<float4*>(dst);
-    for (int f = threadIdx.x; f < nv; f += blockDim.x)
-      d4[f] = make_float4(get_elem<GROUP, STRIDE>(src, 4 * f), get_elem<GROUP, STRIDE>(src, 4 * f + 1),
-                          get_elem<GROUP, STRIDE>(src, 4 * f + 2), get_elem<GROUP, STRIDE>(src, 4 * f + 3));
-    done = nv * 4;
-  }
-  for (int i = done + threadIdx.x; i < count; i += blockDim.x) dst[i] = get_elem<GROUP, STRIDE>(src, i);
-}
-
 template <typename T, int D>
-__global__ void __launch_bounds__(kPreThreads, 3)
+__global__ void __launch_bounds__(kPreThreads)
 k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, GradPtrs gp) {
-  constexpr int K = (D + 1) * (D + 1), SHS = 3 * K + 1;
-  __shared__ float s_sh[kPreThreads * SHS];   // coefficients in, their gradients out
-  __shared__ float s_m[kPreThreads * 3], s_s[kPreThreads * 3], s_o[kPreThreads];
-  __shared__ float s_gm[kPreThreads * 3], s_gs[kPreThreads * 3], s_gq[kPreThreads * 4];
+  constexpr int K = (D + 1) * (D + 1);
   const uint32_t* key = at<uint32_t>(ws, L.key);
   const float4* g2d = at<float4>(ws, L.grad2d);
   const float lp = fd->lowpass;
@@ -475,26 +446,34 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
     const ViewDev& V = fd->views[ch.view];
     const SceneDev& S = fd->scenes[V.scene];
     if (S.dtype != dtype_code<T>() || S.sh_degree != D) continue;
+    const int t = threadIdx.x;
+    if (t >= ch.n) continue;
     const gs_scene_grads& Dg = gp.g[V.scene];
     const bool store = S.n_views == 1;  // else the buffers were zeroed and we add
-    __syncthreads();
-    stage<T, 3, 3>(static_cast<const T*>(S.means) + 3 * ch.g0, 3 * ch.n, s_m);
-    stage<T, 3, 3>(static_cast<const T*>(S.scales) + 3 * ch.g0, 3 * ch.n, s_s);
-    stage<T, 3 * K, SHS>(static_cast<const T*>(S.sh) + 3 * K * ch.g0, 3 * K * ch.n, s_sh);
-    __syncthreads();
-    const int t = threadIdx.x;
-    float* sh = s_sh + t * SHS;
+    auto put = [&](float* dst, int64_t i, float v) {
+      if (store) dst[i] = v;
+      else if (v != 0.f) atomicAdd(dst + i, v);
+    };
+    const int64_t e = ch.e0 + t, g = ch.g0 + t;
     float gm[3] = {0.f, 0.f, 0.f}, gsc[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, go = 0.f;
-    const int64_t e = ch.e0 + t;
-    if (t < ch.n && key[e] == kInvalidKey) {
+    if (key[e] == kInvalidKey) {
+      if (store && Dg.dsh) {
+        float* dst = Dg.dsh + 3 * K * g;
+        if ((3 * K) % 4 == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
 #pragma unroll
-      for (int j = 0; j < 3 * K; ++j) sh[j] = 0.f;
-    } else if (t < ch.n) {
-      float m[3], s[3], q[4];
-      for (int k = 0; k < 3; ++k) { m[k] = s_m[3 * t + k]; s[k] = s_s[3 * t + k]; }
-      load_quat<T>(static_cast<const T*>(S.quats), ch.g0 + t, q);
-      Geo g;
-      geo_forward(V, m, s, q, lp, g);
+          for (int f = 0; f < 3 * K / 4; ++f) reinterpret_cast<float4*>(dst)[f] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+          for (int j = 0; j < 3 * K; ++j) dst[j] = 0.f;
+        }
+      }
+    } else {
+      float m[3], s[3], q[4], o;
+      load_gauss<T>(S, g, m, s, q, o);
+      float c[3 * K];
+      load_sh<T, K>(S, g, c);
+      Geo geo;
+      geo_forward(V, m, s, q, lp, geo);
+      const Geo& gg = geo;
       const float4 ga = g2d[4 * e], gb4 = g2d[4 * e + 1], gc4 = g2d[4 * e + 2], gd4 = g2d[4 * e + 3];
       const float gu = ga.x, gv = ga.y, gca = ga.z, gcb = ga.w;
       const float gcc = gb4.x, gz = gb4.w;
@@ -514,64 +493,81 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
 #pragma unroll
         for (int j = 0; j < K; ++j)
 #pragma unroll
-          for (int k = 0; k < 3; ++k) val[k] += Y[j] * sh[3 * j + k];
+          for (int k = 0; k < 3; ++k) val[k] += Y[j] * c[3 * j + k];
         float gval[3];
         for (int k = 0; k < 3; ++k) gval[k] = val[k] > 0.f ? grgb[k] : 0.f;
         float gdir[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-          const float gY = sh[3 * j] * gval[0] + sh[3 * j + 1] * gval[1] + sh[3 * j + 2] * gval[2];
+          const float gY = c[3 * j] * gval[0] + c[3 * j + 1] * gval[1] +
+                           c[3 * j + 2] * gval[2];
           gdir[0] += gY * dY[j][0]; gdir[1] += gY * dY[j][1]; gdir[2] += gY * dY[j][2];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) sh[3 * j + k] = Y[j] * gval[k];
         }
         float dd = dir[0] * gdir[0] + dir[1] * gdir[1] + dir[2] * gdir[2];
         for (int k = 0; k < 3; ++k) gm[k] += (gdir[k] - dir[k] * dd) * il;
+        // dL/dc_jk = Y_j gval_k
+        if (Dg.dsh) {
+          float* dst = Dg.dsh + 3 * K * g;
+          if (store && (3 * K) % 4 == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+            for (int f = 0; f < 3 * K / 4; ++f) {
+              float v4[4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c) v4[c] = Y[(4 * f + c) / 3] * gval[(4 * f + c) % 3];
+              reinterpret_cast<float4*>(dst)[f] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+#pragma unroll
+              for (int k = 0; k < 3; ++k) put(dst, 3 * j + k, Y[j] * gval[k]);
+          }
+        }
       }
       // ---- p = (z/t) q -----------------------------------------------------------
-      const float it = 1.f / g.tc;
-      const float zt = g.z * it;
+      const float it = 1.f / gg.tc;
+      const float zt = gg.z * it;
       float gq0 = zt * gp0, gq1 = zt * gp1;
-      const float qgp = g.q0 * gp0 + g.q1 * gp1;
+      const float qgp = gg.q0 * gp0 + gg.q1 * gp1;
       const float gz_tot = gz + qgp * it;
-      const float gtc = -g.z * it * it * qgp;
+      const float gtc = -gg.z * it * it * qgp;
       // ---- n = mv / |mv|, mv = -(q0 J0 + q1 J1 + J2) ---------------------------------
-      const float ndg = g.n[0] * gn[0] + g.n[1] * gn[1] + g.n[2] * gn[2];
-      const float iml = 1.f / g.mlen;
+      const float ndg = gg.n[0] * gn[0] + gg.n[1] * gn[1] + gg.n[2] * gn[2];
+      const float iml = 1.f / gg.mlen;
       float gmv[3];
-      for (int k = 0; k < 3; ++k) gmv[k] = (gn[k] - g.n[k] * ndg) * iml;
-      gq0 += -(g.j00 * gmv[0] + g.j02 * gmv[2]);
-      gq1 += -(g.j11 * gmv[1] + g.j12 * gmv[2]);
-      float gj00 = -g.q0 * gmv[0], gj02 = -g.q0 * gmv[2];
-      float gj11 = -g.q1 * gmv[1], gj12 = -g.q1 * gmv[2];
+      for (int k = 0; k < 3; ++k) gmv[k] = (gn[k] - gg.n[k] * ndg) * iml;
+      gq0 += -(gg.j00 * gmv[0] + gg.j02 * gmv[2]);
+      gq1 += -(gg.j11 * gmv[1] + gg.j12 * gmv[2]);
+      float gj00 = -gg.q0 * gmv[0], gj02 = -gg.q0 * gmv[2];
+      float gj11 = -gg.q1 * gmv[1], gj12 = -gg.q1 * gmv[2];
       float gJ2[3] = {-gmv[0], -gmv[1], -gmv[2]};
       // ---- q = -C b --------------------------------------------------------------------
-      const float gca_t = gca - gq0 * g.b0;
-      const float gcb_t = gcb - (gq0 * g.b1 + gq1 * g.b0);
-      const float gcc_t = gcc - gq1 * g.b1;
-      const float gb0 = -(g.ca * gq0 + g.cb * gq1);
-      const float gb1 = -(g.cb * gq0 + g.cc * gq1);
+      const float gca_t = gca - gq0 * gg.b0;
+      const float gcb_t = gcb - (gq0 * gg.b1 + gq1 * gg.b0);
+      const float gcc_t = gcc - gq1 * gg.b1;
+      const float gb0 = -(gg.ca * gq0 + gg.cb * gq1);
+      const float gb1 = -(gg.cb * gq0 + gg.cc * gq1);
       // ---- C = A^-1: dA = -C dC C (symmetric, off-diagonal counted once) ---------------
       const float h = 0.5f * gcb_t;
-      const float X00 = g.ca * gca_t + g.cb * h, X01 = g.ca * h + g.cb * gcc_t;
-      const float X10 = g.cb * gca_t + g.cc * h, X11 = g.cb * h + g.cc * gcc_t;
-      const float gA00 = -(X00 * g.ca + X01 * g.cb);
-      const float gA01 = -(X00 * g.cb + X01 * g.cc);
-      const float gA11 = -(X10 * g.cb + X11 * g.cc);
+      const float X00 = gg.ca * gca_t + gg.cb * h, X01 = gg.ca * h + gg.cb * gcc_t;
+      const float X10 = gg.cb * gca_t + gg.cc * h, X11 = gg.cb * h + gg.cc * gcc_t;
+      const float gA00 = -(X00 * gg.ca + X01 * gg.cb);
+      const float gA01 = -(X00 * gg.cb + X01 * gg.cc);
+      const float gA11 = -(X10 * gg.cb + X11 * gg.cc);
       // ---- Sigma' = G G^T ----------------------------------------------------------------
       const float gS01 = 2.f * gA01;
       float gG[3][3];
       for (int k = 0; k < 3; ++k) {
-        gG[0][k] = 2.f * gA00 * g.G[0][k] + gS01 * g.G[1][k] + gb0 * g.G[2][k];
-        gG[1][k] = 2.f * gA11 * g.G[1][k] + gS01 * g.G[0][k] + gb1 * g.G[2][k];
-        gG[2][k] = gb0 * g.G[0][k] + gb1 * g.G[1][k];
+        gG[0][k] = 2.f * gA00 * gg.G[0][k] + gS01 * gg.G[1][k] + gb0 * gg.G[2][k];
+        gG[1][k] = 2.f * gA11 * gg.G[1][k] + gS01 * gg.G[0][k] + gb1 * gg.G[2][k];
+        gG[2][k] = gb0 * gg.G[0][k] + gb1 * gg.G[1][k];
       }
       // ---- G = T M --------------------------------------------------------------------------
       float gT[3][3], gM[3][3];
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-          gT[i][j] = gG[i][0] * g.M[j][0] + gG[i][1] * g.M[j][1] + gG[i][2] * g.M[j][2];
-          gM[i][j] = g.T[0][i] * gG[0][j] + g.T[1][i] * gG[1][j] + g.T[2][i] * gG[2][j];
+          gT[i][j] = gG[i][0] * gg.M[j][0] + gG[i][1] * gg.M[j][1] + gG[i][2] * gg.M[j][2];
+          gM[i][j] = gg.T[0][i] * gG[0][j] + gg.T[1][i] * gG[1][j] + gg.T[2][i] * gG[2][j];
         }
       // ---- T = J W ----------------------------------------------------------------------------
       for (int k = 0; k < 3; ++k) {
@@ -586,12 +582,12 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
       // ---- M = Rq diag(s) ----------------------------------------------------------------------
       float gR[3][3];
       for (int k = 0; k < 3; ++k) {
-        gsc[k] = gM[0][k] * g.Rq[0][k] + gM[1][k] * g.Rq[1][k] + gM[2][k] * g.Rq[2][k];
+        gsc[k] = gM[0][k] * gg.Rq[0][k] + gM[1][k] * gg.Rq[1][k] + gM[2][k] * gg.Rq[2][k];
         for (int i = 0; i < 3; ++i) gR[i][k] = gM[i][k] * s[k];
       }
       // ---- Rq(qn) and normalisation --------------------------------------------------------------
       {
-        const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
+        const float w = gg.qn[0], x = gg.qn[1], y = gg.qn[2], z = gg.qn[3];
         float gqn[4];
         gqn[0] = 2.f * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
         gqn[1] = 2.f * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2.f * x * gR[1][1] - w * gR[1][2] +
@@ -601,41 +597,36 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
         gqn[3] = 2.f * (-2.f * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] - 2.f * z * gR[1][1] +
                         y * gR[1][2] + x * gR[2][0] + y * gR[2][1]);
         const float qd = w * gqn[0] + x * gqn[1] + y * gqn[2] + z * gqn[3];
-        const float iq = 1.f / g.qnorm;
-        for (int k = 0; k < 4; ++k) gq[k] = (gqn[k] - g.qn[k] * qd) * iq;
+        const float iq = 1.f / gg.qnorm;
+        for (int k = 0; k < 4; ++k) gq[k] = (gqn[k] - gg.qn[k] * qd) * iq;
       }
       // ---- J(x_c), t_c, u, v, z --------------------------------------------------------------------
       float gx[3] = {0.f, 0.f, 0.f};
-      const float iz = g.iz, iz2 = iz * iz;
+      const float iz = gg.iz, iz2 = iz * iz;
       gx[2] += -V.fx * iz2 * gj00 - V.fy * iz2 * gj11;
-      if (!g.clx) {   // j02 = -fx x / z^2
+      if (!gg.clx) {   // j02 = -fx x / z^2
         gx[0] += -V.fx * iz2 * gj02;
-        gx[2] += 2.f * V.fx * g.xc[0] * iz2 * iz * gj02;
+        gx[2] += 2.f * V.fx * gg.xc[0] * iz2 * iz * gj02;
       } else {        // j02 = -fx L / z
-        gx[2] += V.fx * g.txc * iz2 * gj02;
+        gx[2] += V.fx * gg.txc * iz2 * gj02;
       }
-      if (!g.cly) {
+      if (!gg.cly) {
         gx[1] += -V.fy * iz2 * gj12;
-        gx[2] += 2.f * V.fy * g.xc[1] * iz2 * iz * gj12;
+        gx[2] += 2.f * V.fy * gg.xc[1] * iz2 * iz * gj12;
       } else {
-        gx[2] += V.fy * g.tyc * iz2 * gj12;
+        gx[2] += V.fy * gg.tyc * iz2 * gj12;
       }
-      const float jd = g.J2[0] * gJ2[0] + g.J2[1] * gJ2[1] + g.J2[2] * gJ2[2];
-      for (int k = 0; k < 3; ++k) gx[k] += (gJ2[k] - g.J2[k] * jd) * it + gtc * g.J2[k];
+      const float jd = gg.J2[0] * gJ2[0] + gg.J2[1] * gJ2[1] + gg.J2[2] * gJ2[2];
+      for (int k = 0; k < 3; ++k) gx[k] += (gJ2[k] - gg.J2[k] * jd) * it + gtc * gg.J2[k];
       gx[0] += gu * V.fx * iz;
       gx[1] += gv * V.fy * iz;
-      gx[2] += -(gu * V.fx * g.xc[0] + gv * V.fy * g.xc[1]) * iz2 + gz_tot;
+      gx[2] += -(gu * V.fx * gg.xc[0] + gv * V.fy * gg.xc[1]) * iz2 + gz_tot;
       for (int k = 0; k < 3; ++k) gm[k] += V.R[k] * gx[0] + V.R[3 + k] * gx[1] + V.R[6 + k] * gx[2];
     }
-    for (int k = 0; k < 3; ++k) { s_gm[3 * t + k] = gm[k]; s_gs[3 * t + k] = gsc[k]; }
-    for (int k = 0; k < 4; ++k) s_gq[4 * t + k] = gq[k];
-    s_o[t] = go;
-    __syncthreads();
-    unstage<3, 3>(s_gm, 3 * ch.n, Dg.dmeans ? Dg.dmeans + 3 * ch.g0 : nullptr, store);
-    unstage<3, 3>(s_gs, 3 * ch.n, Dg.dscales ? Dg.dscales + 3 * ch.g0 : nullptr, store);
-    unstage<4, 4>(s_gq, 4 * ch.n, Dg.dquats ? Dg.dquats + 4 * ch.g0 : nullptr, store);
-    unstage<1, 1>(s_o, ch.n, Dg.dopacities ? Dg.dopacities + ch.g0 : nullptr, store);
-    unstage<3 * K, SHS>(s_sh, 3 * K * ch.n, Dg.dsh ? Dg.dsh + 3 * K * ch.g0 : nullptr, store);
+    if (Dg.dmeans) for (int k = 0; k < 3; ++k) put(Dg.dmeans, 3 * g + k, gm[k]);
+    if (Dg.dscales) for (int k = 0; k < 3; ++k) put(Dg.dscales, 3 * g + k, gsc[k]);
+    if (Dg.dquats) for (int k = 0; k < 4; ++k) put(Dg.dquats, 4 * g + k, gq[k]);
+    if (Dg.dopacities) put(Dg.dopacities, g, go);
   }
 }
 
@@ -644,28 +635,30 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
 // ---------------------------------------------------------------------------
 static int grid_chunks(int n_chunks) {
   int b = n_chunks < 1 ? 1 : n_chunks;
-  return b > 148 * 16 ? 148 * 16 : b;
+  return b > 148 * 32 ? 148 * 32 : b;
 }
 
 template <typename T>
-static void launch_fwd_t(int deg, const FrameDev* fd, void* ws, const Layout& L, int grid, cudaStream_t s) {
+static cudaError_t fwd_t(int deg, const FrameDev* fd, void* ws, const Layout& L, int grid, cudaStream_t s) {
   switch (deg) {
     case 0: k_preprocess<T, 0><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
     case 1: k_preprocess<T, 1><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
     case 2: k_preprocess<T, 2><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
     default: k_preprocess<T, 3><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
   }
+  return cudaGetLastError();
 }
 
 template <typename T>
-static void launch_bwd_t(int deg, const FrameDev* fd, void* ws, const Layout& L, const GradPtrs& gp,
-                         int grid, cudaStream_t s) {
+static cudaError_t bwd_t(int deg, const FrameDev* fd, void* ws, const Layout& L, const GradPtrs& gp, int grid,
+                         cudaStream_t s) {
   switch (deg) {
     case 0: k_preprocess_bwd<T, 0><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
     case 1: k_preprocess_bwd<T, 1><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
     case 2: k_preprocess_bwd<T, 2><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
     default: k_preprocess_bwd<T, 3><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
   }
+  return cudaGetLastError();
 }
 
 // Bit (4 * dtype + degree) set for every kind of scene that a view renders.
@@ -682,11 +675,12 @@ cudaError_t launch_preprocess(void* ws, const Layout& L, const FrameDev& hf, cud
   const FrameDev* fd = at<FrameDev>(ws, L.frame);
   const unsigned k = kinds(hf);
   const int grid = grid_chunks(hf.n_chunks);
-  for (int deg = 0; deg < 4; ++deg) {
-    if (k & (1u << (4 * GS_F32 + deg))) launch_fwd_t<float>(deg, fd, ws, L, grid, s);
-    if (k & (1u << (4 * GS_BF16 + deg))) launch_fwd_t<__nv_bfloat16>(deg, fd, ws, L, grid, s);
+  cudaError_t e = cudaSuccess;
+  for (int deg = 0; deg < 4 && e == cudaSuccess; ++deg) {
+    if (k & (1u << (4 * GS_F32 + deg))) e = fwd_t<float>(deg, fd, ws, L, grid, s);
+    if (e == cudaSuccess && (k & (1u << (4 * GS_BF16 + deg)))) e = fwd_t<__nv_bfloat16>(deg, fd, ws, L, grid, s);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_preprocess_bwd(void* ws, const Layout& L, const FrameDev& hf, const GradPtrs& gp,
@@ -694,11 +688,12 @@ cudaError_t launch_preprocess_bwd(void* ws, const Layout& L, const FrameDev& hf,
   const FrameDev* fd = at<FrameDev>(ws, L.frame);
   const unsigned k = kinds(hf);
   const int grid = grid_chunks(hf.n_chunks);
-  for (int deg = 0; deg < 4; ++deg) {
-    if (k & (1u << (4 * GS_F32 + deg))) launch_bwd_t<float>(deg, fd, ws, L, gp, grid, s);
-    if (k & (1u << (4 * GS_BF16 + deg))) launch_bwd_t<__nv_bfloat16>(deg, fd, ws, L, gp, grid, s);
+  cudaError_t e = cudaSuccess;
+  for (int deg = 0; deg < 4 && e == cudaSuccess; ++deg) {
+    if (k & (1u << (4 * GS_F32 + deg))) e = bwd_t<float>(deg, fd, ws, L, gp, grid, s);
+    if (e == cudaSuccess && (k & (1u << (4 * GS_BF16 + deg)))) e = bwd_t<__nv_bfloat16>(deg, fd, ws, L, gp, grid, s);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace gs
