@@ -327,7 +327,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
           contrib = true;
           const float4 e2 = my[j][2], e3 = my[j][3];
           const float rgb[3] = {e3.y, e3.z, e3.w}, nrm[3] = {e2.z, e2.w, e3.x};
-          const float ia = 1.f / (1.f - al);
+          const float ia = __fdividef(1.f, 1.f - al);
           T *= ia;                         // transmittance in front of this splat
           const float w = al * T;
           gr[R_R] = w * dC[0]; gr[R_G] = w * dC[1]; gr[R_B] = w * dC[2];
