@@ -56,6 +56,9 @@ typedef enum { GS_F32 = 0, GS_BF16 = 1 } gs_dtype;
 
 enum { GS_MAX_VIEWS = 64, GS_MAX_SCENES = 16 };
 
+/* Size of the device array behind gs_render_fwd_static (32 MiB). */
+#define GS_STATIC_SCRATCH_BYTES (32u << 20)
+
 /* One set of Gaussians (Sec. 3.1).  All arrays are device pointers of the
  * element type `dtype`, contiguous, row-major. */
 typedef struct {
@@ -189,6 +192,33 @@ gs_status gs_preprocess_bwd(const gs_frame* frame, const gs_scene_grads* grads, 
 gs_status gs_debug_copy(const gs_frame* frame, float* rec, int32_t* rect,
                         int32_t* pair_tile, int32_t* pair_entry, int32_t* ranges,
                         float* grad2d, void* stream);
+
+/* Forward render (gs_preprocess, gs_bin, gs_render_fwd) that allocates nothing.
+ *
+ * The paper has no counterpart; this is a convenience of the library.  Some
+ * callers cannot allocate device memory: code that runs inside a host
+ * application which owns the device allocator (a plugin), real-time loops that
+ * forbid allocation once they run, and processes that must not grow their
+ * memory footprint after start-up.  Such callers cannot provide the workspace
+ * the staged calls above need.  Here the workspace is a file-scope device array
+ * of GS_STATIC_SCRATCH_BYTES; every GPU that loads the library holds it until
+ * the process exits.  frame->workspace and frame->workspace_bytes are ignored;
+ * everything else, including pair_capacity, is used as given, and the caller
+ * still provides the scene arrays and the output maps.  A frame whose
+ * workspace would not fit (gs_workspace_size) is rejected with
+ * GS_ERR_INVALID_ARG and a message giving both sizes.
+ *
+ * The first call on a device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  No call runs cudaMalloc, cudaFree or an allocating library
+ * routine.  All calls share the one array and each call re-initialises what
+ * must start at zero (counters, status word, tile ranges), so consecutive calls
+ * are independent; calls whose work overlaps on the GPU (other streams or
+ * threads) race on the array and must be serialised by the caller.  If `stats`
+ * is not NULL the call synchronises `stream` and returns the device status as
+ * gs_check does (a pair overflow leaves the maps unwritten). */
+gs_status gs_render_fwd_static(const gs_frame* frame, const gs_maps* maps, gs_stats* stats,
+                               void* stream);
 
 /* Synchronises `stream`, then reads the counters and sticky status. */
 gs_status gs_check(const gs_frame* frame, gs_stats* out, void* stream);

@@ -67,8 +67,9 @@ class GsStats(Structure):
 
 
 EXPORTS = ("gs_workspace_size", "gs_preprocess", "gs_bin", "gs_render_fwd", "gs_render_bwd",
-           "gs_composite_bwd", "gs_preprocess_bwd", "gs_debug_copy", "gs_check",
-           "gs_last_error_string")
+           "gs_composite_bwd", "gs_preprocess_bwd", "gs_debug_copy", "gs_render_fwd_static",
+           "gs_check", "gs_last_error_string")
+STATIC_SCRATCH_BYTES = 32 << 20
 
 _lib = None
 
@@ -105,6 +106,8 @@ def load(path: str = LIB_PATH):
     lib.gs_debug_copy.argtypes = [pf, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p]
     lib.gs_debug_copy.restype = c_int32
+    lib.gs_render_fwd_static.argtypes = [pf, POINTER(GsMaps), POINTER(GsStats), c_void_p]
+    lib.gs_render_fwd_static.restype = c_int32
     lib.gs_check.argtypes = [pf, POINTER(GsStats), c_void_p]
     lib.gs_check.restype = c_int32
     lib.gs_last_error_string.argtypes = []

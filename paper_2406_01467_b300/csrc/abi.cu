@@ -20,6 +20,14 @@ static gs_status fail(gs_status s, const char* fmt, ...) {
   return s;
 }
 
+gs_status set_error(gs_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
 static gs_status cuda_fail(cudaError_t e, const char* where) {
   return fail(GS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }

@@ -134,6 +134,9 @@ template <> __device__ inline float ldf<__nv_bfloat16>(const __nv_bfloat16* p, i
 
 int tile_sort_bits(int64_t n_tiles);
 
+// Sets the calling thread's error string (printf-style) and returns `s`.
+gs_status set_error(gs_status s, const char* fmt, ...);
+
 // ---- launchers (each .cu file owns its kernels) ---------------------------
 cudaError_t launch_setup(const FrameDev& fd, void* ws, const Layout& L, cudaStream_t s);
 cudaError_t launch_preprocess(void* ws, const Layout& L, const FrameDev& host_fd, cudaStream_t s);
