@@ -166,84 +166,113 @@ k_compact(const uint32_t* __restrict__ key, int64_t E, const uint32_t* __restric
   }
 }
 
-// Emission of (tile, entry) pairs in depth order.  Each warp takes its 32
-// entries of a round together: lane l writes pairs l, l+32, ... of the round's
-// concatenated pair list, finding its entry by a binary search over the warp's
-// inclusive scan, so the stores are contiguous and big splats are shared out.
+// Global exclusive scan of tiles_touched in depth order: pair_off[k] is the
+// first pair of the k-th nearest visible entry.
 __global__ void __launch_bounds__(kSortThreads)
-k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
-       const unsigned long long* n_vis_ptr, int64_t E, const uint32_t* __restrict__ touched,
-       const short4* __restrict__ rect, const uint32_t* __restrict__ blk, int64_t cap,
-       uint32_t* __restrict__ ptile, uint32_t* __restrict__ pval) {
+k_pair_offsets(const uint32_t* __restrict__ sval, const unsigned long long* n_vis_ptr, int64_t E,
+               const uint32_t* __restrict__ touched, const uint32_t* __restrict__ blk,
+               uint32_t* __restrict__ pair_off) {
   __shared__ uint32_t s_wtot[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t n = clamp_count(n_vis_ptr, E);
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   if (base >= n) return;
-  uint32_t ent[kSortItems], cnt[kSortItems];
-#pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    const int64_t i = WarpItems::index(base, r);
-    ent[r] = i < n ? __ldg(sval + i) : 0u;
-  }
+  uint32_t cnt[kSortItems];
   uint32_t wsum = 0;
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    cnt[r] = WarpItems::index(base, r) < n ? __ldg(touched + ent[r]) : 0u;
+    const int64_t i = WarpItems::index(base, r);
+    cnt[r] = i < n ? __ldg(touched + __ldg(sval + i)) : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
     uint32_t x = cnt[r];
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
     wsum += x;
   }
   if (lane == 0) s_wtot[w] = wsum;
   __syncthreads();
-  uint64_t off = blk[blockIdx.x];
+  uint32_t off = blk[blockIdx.x];
   for (int i = 0; i < w; ++i) off += s_wtot[i];
-  const int nv = fd->n_views;
-  const int sx = fd->tile_shift_x, sy = fd->tile_shift_y;
+#pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     uint32_t x = cnt[r];
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(FULL, x, o);
       if (lane >= o) x += y;
     }
-    const uint32_t total = __shfl_sync(FULL, x, 31);
-    // this lane's entry, its first tile and row length, for the others to read
-    const uint32_t e = ent[r];
-    int tx0 = 0, ty0 = 0, nx = 1, rowlen = 0, toff = 0;
-    if (cnt[r]) {
-      const int vi = find_view(fd->entry_off, nv, (int64_t)e);
-      const short4 rc = rect[e];
-      tx0 = rc.x >> sx;
-      ty0 = rc.z >> sy;
-      nx = (rc.y >> sx) - tx0 + 1;
-      rowlen = fd->views[vi].tiles_x;
-      toff = fd->tile_off[vi];
+    const int64_t i = WarpItems::index(base, r);
+    if (i < n) pair_off[i] = off + x - cnt[r];
+    off += __shfl_sync(FULL, x, 31);
+  }
+}
+
+// Last k in [0, n) with off[k] <= p (off is non-decreasing, off[0] = 0).
+__device__ inline int64_t last_le(const uint32_t* off, int64_t n, uint32_t p) {
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Emission of (tile, entry) pairs in depth order, load-balanced over the whole
+// grid: block slice c writes pairs [c * kEmitChunk, (c + 1) * kEmitChunk).  Two
+// binary searches over pair_off give the slice's entry range (at most one
+// entry per pair, so it fits in shared memory); each thread then finds the
+// entry of each of its pairs by a short search there.  Stores are contiguous
+// and a splat covering hundreds of tiles is shared by many threads.
+constexpr int kEmitChunk = 2048;
+
+__global__ void __launch_bounds__(kSortThreads)
+k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
+       const unsigned long long* n_vis_ptr, const unsigned long long* n_pairs_ptr, int64_t E,
+       const short4* __restrict__ rect, const uint32_t* __restrict__ pair_off, int64_t cap,
+       uint32_t* __restrict__ ptile, uint32_t* __restrict__ pval) {
+  __shared__ uint32_t s_off[kEmitChunk + 1], s_ent[kEmitChunk + 1];
+  __shared__ short4 s_rc[kEmitChunk + 1];
+  __shared__ int64_t s_k[2];
+  const int64_t n = clamp_count(n_vis_ptr, E);
+  const int64_t P = clamp_count(n_pairs_ptr, cap);
+  const int nv = fd->n_views;
+  const int sx = fd->tile_shift_x, sy = fd->tile_shift_y;
+  const int tiles_x0 = fd->views[0].tiles_x;
+  for (int64_t p0 = (int64_t)blockIdx.x * kEmitChunk; p0 < P; p0 += (int64_t)gridDim.x * kEmitChunk) {
+    const int64_t p1 = min(P, p0 + kEmitChunk);
+    __syncthreads();
+    if (threadIdx.x < 2) s_k[threadIdx.x] = last_le(pair_off, n, (uint32_t)(threadIdx.x ? p1 - 1 : p0));
+    __syncthreads();
+    const int64_t k0 = s_k[0];
+    const int m = (int)(s_k[1] - k0 + 1);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const uint32_t e = __ldg(sval + k0 + i);
+      s_off[i] = __ldg(pair_off + k0 + i);
+      s_ent[i] = e;
+      s_rc[i] = rect[e];
     }
-    for (uint32_t k0 = 0; k0 < total; k0 += 32) {
-      const uint32_t p = k0 + lane;
-      // owner: first lane whose inclusive count exceeds p
-      int lo = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t xv = __shfl_sync(FULL, x, lo + step - 1);
-        if (xv <= p) lo += step;
+    __syncthreads();
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+      int lo = 0, hi = m - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= (uint32_t)p) lo = mid; else hi = mid - 1;
       }
-      const uint32_t xo = __shfl_sync(FULL, x, lo), co = __shfl_sync(FULL, cnt[r], lo);
-      const uint32_t eo = __shfl_sync(FULL, e, lo);
-      const int tx0o = __shfl_sync(FULL, tx0, lo), ty0o = __shfl_sync(FULL, ty0, lo);
-      const int nxo = __shfl_sync(FULL, nx, lo), rlo = __shfl_sync(FULL, rowlen, lo);
-      const int tofo = __shfl_sync(FULL, toff, lo);
-      if (p < total) {
-        const uint32_t local = p - (xo - co);
-        const uint32_t ty = local / (uint32_t)nxo, tx = local - ty * (uint32_t)nxo;
-        const uint64_t dst = off + p;
-        if (dst < (uint64_t)cap) {
-          ptile[dst] = (uint32_t)(tofo + (ty0o + (int)ty) * rlo + tx0o + (int)tx);
-          pval[dst] = eo;
-        }
+      const uint32_t e = s_ent[lo];
+      const short4 rc = s_rc[lo];
+      const int tx0 = rc.x >> sx, ty0 = rc.z >> sy;
+      const uint32_t nx = (uint32_t)((rc.y >> sx) - tx0 + 1);
+      const uint32_t local = (uint32_t)p - s_off[lo];
+      const uint32_t ty = local / nx, tx = local - ty * nx;
+      int rowlen = tiles_x0, toff = 0;
+      if (nv > 1) {
+        const int vi = find_view(fd->entry_off, nv, (int64_t)e);
+        rowlen = fd->views[vi].tiles_x;
+        toff = fd->tile_off[vi];
       }
+      ptile[p] = (uint32_t)(toff + (ty0 + (int)ty) * rowlen + tx0 + (int)tx);
+      pval[p] = e;
     }
-    off += total;
   }
 }
 
@@ -436,8 +465,11 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   k_block_sums<1><<<L.nb_E, kSortThreads, 0, s>>>(touched, vv0, &hdr->n_vis, L.E, blk);
   k_scan_partials<<<1, 1024, 0, s>>>(blk, L.nb_E, &hdr->n_pairs, L.Pcap, hdr);
   // 4. emission
-  k_emit<<<L.nb_E, kSortThreads, 0, s>>>(fd, vv0, &hdr->n_vis, L.E, touched,
-                                         at<short4>(ws, L.rect), blk, L.Pcap, pt0, pv0);
+  uint32_t* pair_off = at<uint32_t>(ws, L.pair_off);
+  k_pair_offsets<<<L.nb_E, kSortThreads, 0, s>>>(vv0, &hdr->n_vis, L.E, touched, blk, pair_off);
+  const int eg = (int)std::min<int64_t>((L.Pcap + kEmitChunk - 1) / kEmitChunk, 148 * 8);
+  k_emit<<<eg, kSortThreads, 0, s>>>(fd, vv0, &hdr->n_vis, &hdr->n_pairs, L.E, at<short4>(ws, L.rect),
+                                     pair_off, L.Pcap, pt0, pv0);
   // 5. tile sort
   const int bits = tile_sort_bits(L.T);
   err = radix_sort(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, hist, tot, s);
