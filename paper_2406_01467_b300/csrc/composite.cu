@@ -44,13 +44,13 @@ struct TileCtx {
   int64_t pix_base;    // first pixel of the view
 };
 
-__device__ inline TileCtx tile_ctx(const FrameDev* fd, int tile) {
+__device__ inline TileCtx tile_ctx(const FrameDev* fd, int tile, int sub) {
   TileCtx c;
   c.view = find_view_tile(fd->tile_off, fd->n_views, tile);
   const ViewDev& V = fd->views[c.view];
   const int local = tile - fd->tile_off[c.view];
   const int tx = local % V.tiles_x, ty = local / V.tiles_x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = sub, lane = threadIdx.x & 31;
   const int sub_per_row = fd->tile_w / kSubW;
   c.x0 = tx * fd->tile_w;
   c.y0 = ty * fd->tile_h;
@@ -100,8 +100,8 @@ struct SubRect {
   float X0, X1, Y0, Y1;
 };
 
-__device__ inline SubRect sub_rect(int x0, int y0, int sub_per_row) {
-  const int w = threadIdx.x >> 5;
+__device__ inline SubRect sub_rect(int x0, int y0, int sub_per_row, int sub) {
+  const int w = sub;
   SubRect r;
   r.X0 = (float)(x0 + (w % sub_per_row) * kSubW) + 0.5f;
   r.Y0 = (float)(y0 + (w / sub_per_row) * kSubH) + 0.5f;
@@ -116,33 +116,25 @@ __device__ inline bool reaches(const float4& f0, const float4& f1, const SubRect
   return rect_min_sigma(f0.x, f0.y, f0.z, f0.w, f1.x, ia, ic, R.X0, R.X1, R.Y0, R.Y1) <= f1.z;
 }
 
-// Each warp walks its tile's list on its own, 32 records at a time: every lane
-// loads one record's first half and tests it against the warp's rectangle; the
-// records that pass are staged whole in the warp's shared slots and evaluated
-// by all 32 lanes in list order.  No block-wide barrier: a warp leaves as soon
-// as its own pixels are done.
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_maps maps) {
-  constexpr int NW = BLOCK / 32;
-  __shared__ float4 s_rec[NW][32][4];
-  const Header* hdr = at<Header>(ws, L.hdr);
-  if (hdr->status == GS_ERR_CAPACITY) return;
-  const int tile = blockIdx.x;
-  const TileCtx c = tile_ctx(fd, tile);
+// One work item: warp-sized block `sub` of tile `tile`.  The warp walks the
+// tile's list on its own, 32 records at a time: every lane loads one record's
+// first half and tests it against the warp's rectangle; the records that pass
+// are staged whole in the warp's shared slots and evaluated by all 32 lanes in
+// list order.  The walk ends as soon as the block's own pixels are done.
+__device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restrict__ ws, const Layout& L,
+                                const gs_maps& maps, int tile, int sub, float4 (*my)[4], uint32_t& evals) {
+  const TileCtx c = tile_ctx(fd, tile, sub);
   const int2 range = at<int2>(ws, L.ranges)[tile];
   const uint32_t* pval = at<uint32_t>(ws, L.pval_final);
   const float4* rec = at<float4>(ws, L.rec);
   const float amin = fd->alpha_min, amax = fd->alpha_max, tmin = fd->T_min, tmed = fd->median_T;
   const float fpx = c.px + 0.5f, fpy = c.py + 0.5f;
   const int lane = threadIdx.x & 31;
-  const SubRect R = sub_rect(c.x0, c.y0, fd->tile_w / kSubW);
-  float4 (*my)[4] = s_rec[threadIdx.x >> 5];
+  const SubRect R = sub_rect(c.x0, c.y0, fd->tile_w / kSubW, sub);
 
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, depth = 0.f;
   int last = -1, med = -1;
   bool done = !c.inside;
-  uint32_t evals = 0;
   for (int c0 = range.x; c0 < range.y; c0 += 32) {
     if (__all_sync(kFull, done)) break;
     const int i = c0 + lane;
@@ -185,7 +177,6 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     }
     __syncwarp();
   }
-  count_evals(evals, &at<Header>(ws, L.hdr)->n_evals_fwd);
   if (!c.inside) return;
   if (med < 0 && last >= 0) {   // median never reached: depth of the last contributor
     med = last;
@@ -244,16 +235,12 @@ __device__ inline float warp_reduce_scatter16(float (&v)[16]) {
   return v[0] + __shfl_xor_sync(kFull, v[0], 1);
 }
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_map_grads g) {
-  constexpr int NW = BLOCK / 32;
-  __shared__ float4 s_rec[NW][32][4];
-  __shared__ uint32_t s_ent[NW][32];
-  const Header* hdr = at<Header>(ws, L.hdr);
-  if (hdr->status == GS_ERR_CAPACITY) return;
-  const int tile = blockIdx.x;
-  const TileCtx c = tile_ctx(fd, tile);
+// One backward work item (same decomposition as fwd_item): the warp replays
+// its pixels from their last contributors toward the front of the list.
+__device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restrict__ ws, const Layout& L,
+                                const gs_map_grads& g, int tile, int sub, float4 (*my)[4], uint32_t* my_e,
+                                uint32_t& evals) {
+  const TileCtx c = tile_ctx(fd, tile, sub);
   const int2 range = at<int2>(ws, L.ranges)[tile];
   const uint32_t* pval = at<uint32_t>(ws, L.pval_final);
   const float4* rec = at<float4>(ws, L.rec);
@@ -261,9 +248,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
   const float amin = fd->alpha_min, amax = fd->alpha_max;
   const float fpx = c.px + 0.5f, fpy = c.py + 0.5f;
   const int lane = threadIdx.x & 31;
-  const SubRect R = sub_rect(c.x0, c.y0, fd->tile_w / kSubW);
-  float4 (*my)[4] = s_rec[threadIdx.x >> 5];
-  uint32_t* my_e = s_ent[threadIdx.x >> 5];
+  const SubRect R = sub_rect(c.x0, c.y0, fd->tile_w / kSubW, sub);
 
   float Tf = 1.f;
   int last = -1, med = -1;
@@ -288,7 +273,6 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
 
   float T = Tf;
   float Sc[3] = {0.f, 0.f, 0.f}, Sn[3] = {0.f, 0.f, 0.f};
-  uint32_t evals = 0;
   for (int c1 = wmax + 1; c1 > range.x; c1 -= 32) {
     const int i = c1 - 1 - lane;          // lane 0 holds the farthest record of the chunk
     bool rel = false;
@@ -370,42 +354,96 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     }
     __syncwarp();
   }
-  count_evals(evals, &at<Header>(ws, L.hdr)->n_evals_bwd);
+}
+
+// Persistent kernels: every warp pulls work items (tile, 8x4 block) from an
+// atomic counter until the frame is done, so no warp waits for another and the
+// tail is one small item.  The result does not depend on which warp takes
+// which item (each pixel is computed by exactly one warp).
+constexpr int kRenderThreads = 256;
+
+__global__ void __launch_bounds__(kRenderThreads)
+k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_maps maps, int subs,
+             int n_items) {
+  __shared__ float4 s_rec[kRenderThreads / 32][32][4];
+  Header* hdr = at<Header>(ws, L.hdr);
+  if (hdr->status == GS_ERR_CAPACITY) return;
+  float4 (*my)[4] = s_rec[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  uint32_t evals = 0;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(&hdr->work_fwd, 1);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= n_items) break;
+    fwd_item(fd, ws, L, maps, item / subs, item % subs, my, evals);
+    __syncwarp();
+  }
+  count_evals(evals, &hdr->n_evals_fwd);
+}
+
+__global__ void __launch_bounds__(kRenderThreads)
+k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_map_grads g, int subs,
+             int n_items) {
+  __shared__ float4 s_rec[kRenderThreads / 32][32][4];
+  __shared__ uint32_t s_ent[kRenderThreads / 32][32];
+  Header* hdr = at<Header>(ws, L.hdr);
+  if (hdr->status == GS_ERR_CAPACITY) return;
+  float4 (*my)[4] = s_rec[threadIdx.x >> 5];
+  uint32_t* my_e = s_ent[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  uint32_t evals = 0;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(&hdr->work_bwd, 1);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= n_items) break;
+    bwd_item(fd, ws, L, g, item / subs, item % subs, my, my_e, evals);
+    __syncwarp();
+  }
+  count_evals(evals, &hdr->n_evals_bwd);
+}
+
+// A resident wave of blocks for a persistent kernel.
+template <typename K>
+static int persistent_grid(K kernel, int n_items) {
+  int dev = 0, sms = 148, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kRenderThreads, 0);
+  const int need = (n_items + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
+  int g = sms * (per_sm < 1 ? 1 : per_sm);
+  return g < need ? g : (need < 1 ? 1 : need);
 }
 
 cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& hf, const gs_maps& maps,
                               cudaStream_t s) {
   const FrameDev* fd = at<FrameDev>(ws, L.frame);
-  cudaError_t err = cudaMemsetAsync(&at<Header>(ws, L.hdr)->n_evals_fwd, 0, 8, s);
+  Header* hdr = at<Header>(ws, L.hdr);
+  cudaError_t err = cudaMemsetAsync(&hdr->n_evals_fwd, 0, 8, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(&hdr->work_fwd, 0, 4, s);
   if (err != cudaSuccess) return err;
-  const int block = hf.tile_w * hf.tile_h;
-  const int grid = (int)L.T;
-  if (grid == 0) return cudaSuccess;
-  switch (block) {
-    case 64: k_render_fwd<64><<<grid, 64, 0, s>>>(fd, ws, L, maps); break;
-    case 128: k_render_fwd<128><<<grid, 128, 0, s>>>(fd, ws, L, maps); break;
-    case 256: k_render_fwd<256><<<grid, 256, 0, s>>>(fd, ws, L, maps); break;
-    default: return cudaErrorInvalidValue;
-  }
+  if (L.T == 0) return cudaSuccess;
+  const int subs = hf.tile_w * hf.tile_h / 32;
+  const int n_items = (int)L.T * subs;
+  k_render_fwd<<<persistent_grid(k_render_fwd, n_items), kRenderThreads, 0, s>>>(fd, ws, L, maps, subs,
+                                                                                  n_items);
   return cudaGetLastError();
 }
 
 cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& hf, const gs_map_grads& g,
                               cudaStream_t s) {
   const FrameDev* fd = at<FrameDev>(ws, L.frame);
+  Header* hdr = at<Header>(ws, L.hdr);
   cudaError_t err = cudaMemsetAsync(at<float>(ws, L.grad2d), 0,
                                     sizeof(float) * kRecFloats * (size_t)L.E, s);
-  if (err == cudaSuccess) err = cudaMemsetAsync(&at<Header>(ws, L.hdr)->n_evals_bwd, 0, 8, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(&hdr->n_evals_bwd, 0, 8, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(&hdr->work_bwd, 0, 4, s);
   if (err != cudaSuccess) return err;
-  const int block = hf.tile_w * hf.tile_h;
-  const int grid = (int)L.T;
-  if (grid == 0) return cudaSuccess;
-  switch (block) {
-    case 64: k_render_bwd<64><<<grid, 64, 0, s>>>(fd, ws, L, g); break;
-    case 128: k_render_bwd<128><<<grid, 128, 0, s>>>(fd, ws, L, g); break;
-    case 256: k_render_bwd<256><<<grid, 256, 0, s>>>(fd, ws, L, g); break;
-    default: return cudaErrorInvalidValue;
-  }
+  if (L.T == 0) return cudaSuccess;
+  const int subs = hf.tile_w * hf.tile_h / 32;
+  const int n_items = (int)L.T * subs;
+  k_render_bwd<<<persistent_grid(k_render_bwd, n_items), kRenderThreads, 0, s>>>(fd, ws, L, g, subs, n_items);
   return cudaGetLastError();
 }
 

@@ -80,7 +80,8 @@ struct Header {
   unsigned long long n_evals_fwd;
   unsigned long long n_evals_bwd;
   int32_t status;
-  int32_t pad_[53];
+  int32_t work_fwd, work_bwd;   // work-queue counters of the persistent compositing kernels
+  int32_t pad_[51];
 };
 
 // Byte offsets of every buffer inside the caller's workspace.
