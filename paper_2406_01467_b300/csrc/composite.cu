@@ -272,6 +272,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
   const int wmax = __reduce_max_sync(kFull, last);
 
   float T = Tf;
+  const float dATf = dA * Tf;
   float Sc[3] = {0.f, 0.f, 0.f}, Sn[3] = {0.f, 0.f, 0.f};
   for (int c1 = wmax + 1; c1 > range.x; c1 -= 32) {
     const int i = c1 - 1 - lane;          // lane 0 holds the farthest record of the chunk
@@ -316,14 +317,16 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
           const float w = al * T;
           gr[R_R] = w * dC[0]; gr[R_G] = w * dC[1]; gr[R_B] = w * dC[2];
           gr[R_N0] = w * dN[0]; gr[R_N1] = w * dN[1]; gr[R_N2] = w * dN[2];
-          const float dal = T * ((rgb[0] - Sc[0]) * dC[0] + (rgb[1] - Sc[1]) * dC[1] + (rgb[2] - Sc[2]) * dC[2] +
-                                 (nrm[0] - Sn[0]) * dN[0] + (nrm[1] - Sn[1]) * dN[1] + (nrm[2] - Sn[2]) * dN[2]) +
-                            dA * Tf * ia;
+          // (x - S) enters both dL/dalpha and the update S += alpha (x - S)
+          float dsum = 0.f;
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            Sc[k] = al * rgb[k] + (1.f - al) * Sc[k];
-            Sn[k] = al * nrm[k] + (1.f - al) * Sn[k];
+            const float dc = rgb[k] - Sc[k], dn = nrm[k] - Sn[k];
+            dsum += dc * dC[k] + dn * dN[k];
+            Sc[k] += al * dc;
+            Sn[k] += al * dn;
           }
+          const float dal = T * dsum + dATf * ia;
           float gu = 0.f, gv = 0.f;
           if (idx == med) {            // d = z_c + p . Delta (Eq. 4)
             gr[R_Z] = dD;
