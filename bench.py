@@ -55,6 +55,31 @@ def make_workload(name):
     return scenes.tiny_scene(c["n"], c["seed"]), scenes.tiny_camera()
 
 
+def load_traffic(config):
+    """DRAM bytes per launch measured by ncu for each stage's kernel, or None for
+    a stage whose kernel source changed since the capture (or another workload)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "dram_traffic_unbounded_3M_1297x840.json")
+    if config != "unbounded" or not os.path.exists(p):
+        return {}
+    with open(p) as f:
+        d = json.load(f)
+    csrc = os.path.join(ROOT, "paper_2406_01467_b300", "csrc")
+
+    def digest(name):
+        m = hashlib.sha256()
+        for fn in (name, "gs_internal.cuh"):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                m.update(fh.read())
+        return m.hexdigest()[:16]
+
+    out = {}
+    for stage, rec in d["bytes_per_launch"].items():
+        if digest(rec["source"]) == d["source_sha256_16"].get(rec["source"]):
+            out[stage] = int(rec["bytes"])
+    return out
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -275,10 +300,12 @@ def run_ours(args, rank, world, device):
             roof[k] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
                        "unit": "Tops/s", "frac": round(ach / alu_peak, 4), "ops": int(work),
                        "ms": round(stages[k], 4)}
+    traffic = load_traffic(args.config)
+    for k in roof:
+        roof[k]["traffic"] = traffic.get(k)
     dom = max(stages, key=lambda k: stages[k])
     r = dict(roof[dom])
     r["kernel"] = dom
-    r["traffic"] = None
     r["peak_source"] = f"{src} ({'MEASURED_PEAKS.json' if src == 'measured' else 'recipe fallback'})"
     out = {
         "metric": METRIC, "value": round(ms, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
