@@ -327,6 +327,79 @@ def frame_tiles(cam, p):
 
 
 # --------------------------------------------------------------------------------------
+# extra lines: BF16 storage under a CUDA graph, and the batched many-view frame
+# --------------------------------------------------------------------------------------
+def timed_graph(step, steps, warmup):
+    import torch
+    from paper_2406_01467_b300 import autotune
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    eager = autotune.time_step(step, max(3, steps // 4))
+    g = autotune.capture(step)
+    ms = autotune.time_step(g.replay, steps)
+    return ms, eager
+
+
+def run_bf16(args, device):
+    """The 3M scene with every parameter stored in BF16 (FP32 compositing), whole
+    forward + backward captured in one CUDA graph."""
+    import torch
+    from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, autotune, scenes
+    scene, cam = make_workload("unbounded")
+    st = SceneTensors.from_scene(scene, device, torch.bfloat16)
+    fr = Frame([st], [(cam, 0)], RenderParams())
+    fr.forward()
+    need = int(fr.stats().n_pairs)
+    fr._alloc(int(need * 1.25) + 1024)
+    up = [torch.from_numpy(u[0]).to(device) for u in scenes.upstream_grads(11, cam.height, cam.width)]
+    step = autotune.make_step(fr, up, fr.alloc_grads())
+    ms, eager = timed_graph(step, args.steps, args.warmup)
+    fr.stats()
+    if fr.last_status != 0:
+        raise RuntimeError(f"bf16 frame status {fr.last_status}")
+    return {"workload": "unbounded scene, 3M Gaussians, BF16 storage, FP32 compositing, 1297x840",
+            "ms_per_step_graph": round(ms, 4), "ms_per_step_eager": round(eager, 4),
+            "param_bytes": int(sum(getattr(st, k).numel() * 2 for k in ("means", "scales", "quats", "opacities", "sh")))}
+
+
+def batched_workload():
+    """A 1M-Gaussian unbounded scene seen from 16 orbit views of uneven sizes,
+    plus four object scenes (50K/200K/800K/2M) with one 800x600 view each."""
+    from paper_2406_01467_b300 import scenes
+    big = scenes.unbounded_scene(1_000_000, seed=3)
+    objs = [scenes.object_scene(n, seed=5 + i) for i, n in enumerate((50_000, 200_000, 800_000, 2_000_000))]
+    views = [(c, 0) for c in scenes.orbit_cameras(16, seed=4)]
+    views += [(scenes.object_camera(), 1 + i) for i in range(4)]
+    return [big] + objs, views
+
+
+def run_batched(args, device):
+    import torch
+    from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, autotune
+    sc, views = batched_workload()
+    sts = [SceneTensors.from_scene(x, device) for x in sc]
+    params, report = autotune.tune_tile(sts, views, RenderParams(), iters=3, cache_path=None)
+    fr = Frame(sts, views, params)
+    fr.forward()
+    need = int(fr.stats().n_pairs)
+    fr._alloc(int(need * 1.25) + 1024)
+    g = torch.Generator(device=device).manual_seed(12)
+    up = [torch.randn(k * fr.n_pixels, device=device, generator=g) for k in (3, 1, 1, 3)]
+    step = autotune.make_step(fr, up, fr.alloc_grads())
+    ms, eager = timed_graph(step, max(10, args.steps // 4), args.warmup)
+    st = fr.stats()
+    if fr.last_status != 0:
+        raise RuntimeError(f"batched frame status {fr.last_status}")
+    return {"workload": "16 views (512..1600 x 384..1200) of a 1M unbounded scene + 4 object scenes "
+                        "(50K/200K/800K/2M, 800x600), FP32, one launch per kernel",
+            "views": len(views), "scenes": len(sts), "entries": int(st.n_entries), "pixels": int(fr.n_pixels),
+            "pairs": int(st.n_pairs), "tile": f"{params.tile_w}x{params.tile_h}", "autotune_ms": report["all"],
+            "ms_per_batch_graph": round(ms, 4), "ms_per_batch_eager": round(eager, 4),
+            "ms_per_view_graph": round(ms / len(views), 4)}
+
+
+# --------------------------------------------------------------------------------------
 # CPU oracle (baseline arm and cpu_baseline field)
 # --------------------------------------------------------------------------------------
 def oracle_sample(scene, cam, crop=32, n_crops=1, seed=0):
@@ -399,6 +472,7 @@ def main():
     ap.add_argument("--config", choices=list(CONFIGS), default="unbounded")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the BF16 and batched lines")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -418,6 +492,9 @@ def main():
         torch.cuda.set_device(local)
         tdist.init_process_group("nccl")
     out = run_ours(args, rank, world, f"cuda:{local}")
+    if not args.no_extras and args.config == "unbounded":
+        out["bf16_graph"] = run_bf16(args, f"cuda:{local}")
+        out["batched"] = run_batched(args, f"cuda:{local}")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         scene, cam = make_workload(args.config)
         est, secs, cores, sample = oracle_sample(scene, cam, n_crops=16)

@@ -1,0 +1,88 @@
+"""CUDA-graph capture of a whole forward + backward step, the tile autotuner, and
+the BF16-storage accuracy on the 3M-Gaussian frame (error against the FP64
+oracle on a central 128x128 crop)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, autotune, scenes
+from tests._util import AMBIG_MARGIN, compare_maps, gpu_maps_at, oracle_params
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _setup(sc, cam, p=None, dtype=torch.float32):
+    st = SceneTensors.from_scene(sc, DEV, dtype)
+    fr = Frame([st], [(cam, 0)], p or RenderParams())
+    fr.forward()
+    fr._alloc(int(fr.stats().n_pairs * 1.25) + 1024)
+    up = [torch.from_numpy(u[0]).to(DEV) for u in scenes.upstream_grads(3, cam.height, cam.width)]
+    return fr, up
+
+
+def test_graph_replay_matches_eager_step():
+    sc, cam = scenes.object_scene(30_000, seed=9), scenes.object_camera(400, 300, 550.0)
+    fr, up = _setup(sc, cam)
+    grads = fr.alloc_grads()
+    step = autotune.make_step(fr, up, grads)
+    step()
+    torch.cuda.synchronize()
+    maps0 = [t.clone() for t in fr.view_maps(0)]
+    g0 = {k: v.clone() for k, v in grads[0].items()}
+    graph = autotune.capture(step)
+    for _ in range(2):
+        for t in list(fr.view_maps(0)) + list(grads[0].values()):
+            t.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        for a, b in zip(fr.view_maps(0), maps0):
+            torch.testing.assert_close(a, b, rtol=0, atol=0)
+        for k in g0:   # float atomics: equal up to summation order
+            torch.testing.assert_close(grads[0][k], g0[k], rtol=1e-4, atol=1e-6 * g0[k].abs().max().item())
+    assert fr.stats().status == 0
+
+
+def test_autotuner_returns_a_candidate_and_caches_it(tmp_path):
+    sc, cam = scenes.object_scene(20_000, seed=10), scenes.object_camera(320, 240, 440.0)
+    st = SceneTensors.from_scene(sc, DEV)
+    cache = str(tmp_path / "tiles.json")
+    cands = ((16, 16), (8, 8), (16, 8))
+    p, rep = autotune.tune_tile([st], [(cam, 0)], RenderParams(), candidates=cands, iters=2, cache_path=cache)
+    assert (p.tile_w, p.tile_h) in cands and not rep["cached"] and len(rep["all"]) == 3
+    p2, rep2 = autotune.tune_tile([st], [(cam, 0)], RenderParams(), candidates=cands, cache_path=cache)
+    assert rep2["cached"] and (p2.tile_w, p2.tile_h) == (p.tile_w, p.tile_h)
+
+
+@pytest.mark.slow
+def test_bf16_storage_error_on_central_crop():
+    # The 3M / 1297x840 frame with BF16 parameters.  (i) against the oracle fed
+    # the same BF16-rounded parameters: compute precision, FP32 tolerances;
+    # (ii) against the oracle fed the FP32 parameters: storage quantisation,
+    # reported (BF16's 8-bit mantissa moves far splats by decimetres).
+    sc, cam = scenes.unbounded_scene(), scenes.unbounded_camera()
+    p = RenderParams()
+    fr, _ = _setup(sc, cam, p, torch.bfloat16)
+    ys, xs = np.mgrid[356:484, 584:712]
+    pix = (ys * cam.width + xs).reshape(-1)
+    r = scenes.to_bf16_rounded
+    sc_r = scenes.Scene(r(sc.means), r(sc.scales), r(sc.quats), r(sc.opacities), r(sc.sh), sc.sh_degree)
+    op = oracle_params(p)
+    gpu = gpu_maps_at(fr, pix)
+
+    def near_crop(s):   # the Gaussians whose rectangles reach the crop (same order)
+        from oracle import binning
+        d = binning.decide(s.means, s.scales, s.quats, s.opacities, cam, op)
+        rc = d["rect"]
+        sel = d["valid"] & (rc[:, 1] >= 584) & (rc[:, 0] <= 711) & (rc[:, 3] >= 356) & (rc[:, 2] <= 483)
+        return s.subset(np.nonzero(sel)[0])
+
+    ref_r = oracle.render(near_crop(sc_r), cam, op, pixels=pix)
+    bad, rep = compare_maps(gpu, ref_r, ref_r["margin"])
+    assert rep["n_bad"] == 0, rep
+    ref_f = oracle.render(near_crop(sc), cam, op, pixels=pix)
+    errs = {k: float(np.abs(g - ref_f[k]).max()) for g, k in zip(gpu, ("color", "alpha", "depth", "normal"))}
+    print("bf16 compute error (same rounded inputs):", rep)
+    print("bf16 storage error (fp32 inputs):", errs)
+    assert all(np.isfinite(v) for v in errs.values())
