@@ -141,6 +141,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value, device):
+    """The largest value over all ranks (the value itself without a process group)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def launches_per_step(n_tiles, n_dtypes=1):
     """Kernels libgs launches for one preprocess + bin + fwd + bwd (memsets excluded)."""
     bits = max(1, int(np.ceil(np.log2(max(n_tiles, 2)))))
@@ -219,11 +230,7 @@ def run_ours(args, rank, world, device):
         stages["composite_bwd"] += ev[3].elapsed_time(ev[4])
         stages["preprocess_bwd"] += ev[4].elapsed_time(ev[5])
     stages = {k: v / args.steps for k, v in stages.items()}
-    ms = ms_total / args.steps
-    if dist:
-        t = torch.tensor([ms], device=device)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms_total / args.steps, device)
 
     # ---- end to end: host parameters in, host maps and gradients out --------------------
     e2e = None
@@ -255,11 +262,7 @@ def run_ours(args, rank, world, device):
             e2e_step()
         b.record()
         torch.cuda.synchronize()
-        e2e_ms = a.elapsed_time(b) / n_e2e
-        if dist:
-            t = torch.tensor([e2e_ms], device=device)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(a.elapsed_time(b) / n_e2e, device)
         e2e = {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
 
