@@ -6,7 +6,9 @@
  * 2406.01467), the alpha map, the rasterized planar depth map (Eq. 4 with the
  * plane coefficients of Eq. 13-17 and the median rule of Sec. 1) and the normal
  * map (Eq. 18-22), and the gradients of a loss on those maps with respect to
- * the Gaussian parameters.
+ * the Gaussian parameters.  Optionally it also renders the two per-pixel
+ * geometric regularisers of Sec. 3.4 -- the depth distortion L_d (Eq. 23) and
+ * the normal consistency L_n (Eq. 24) -- and their gradients.
  *
  * Conventions
  *   - camera frame: +x right, +y down, +z forward; viewmat is the row-major 4x4
@@ -91,6 +93,10 @@ typedef struct {
   float T_min;            /* in [0, 1): stop before T would fall below it */
   float median_T;         /* in (0, 1): median depth threshold on T */
   float clamp_margin;     /* x/z, y/z inside J clamped to the image widened by this */
+  int32_t losses;         /* 0 or 1.  1 keeps, per pixel, the state that the loss maps
+                             of Eq. 23-24 and their backward need (10 floats per pixel
+                             of workspace); with 0, gs_maps.dist / nloss and
+                             gs_map_grads.ddist / dnloss must be NULL */
 } gs_params;
 
 /* Everything a call needs to know about one frame (a batch of views). */
@@ -105,20 +111,42 @@ typedef struct {
   size_t workspace_bytes;
 } gs_frame;
 
-/* Output maps (device, FP32), all views concatenated. */
+/* Output maps (device, FP32), all views concatenated.  Any pointer may be NULL
+ * (that map is not written).
+ *
+ * dist (Eq. 23): sum over ordered pairs (i, j) of the splats blended at the
+ *   pixel of w_i w_j (d_i - d_j)^2, with w the blending weights alpha_i T_i and
+ *   d_i the planar depth of splat i at the pixel (Eq. 4).
+ * nloss (Eq. 24): sum_i w_i (1 - n_i . n~) = alpha - normal . n~, where n~ is
+ *   the unit normal of the depth map back-projected to camera space,
+ *   P(i, j) = depth(i, j) ((i + 1/2 - cx)/fx, (j + 1/2 - cy)/fy, 1),
+ *   n~ = normalize((P(i, j+1) - P(i, j-1)) x (P(i+1, j) - P(i-1, j))).  It is
+ *   defined at pixels not on the image border whose alpha and whose four
+ *   neighbours' alphas are > 0 (and where that cross product is not zero);
+ *   elsewhere nloss is 0.  Both need params.losses = 1. */
 typedef struct {
   float* color;  /* [sum_v 3 H_v W_v] */
   float* alpha;  /* [sum_v H_v W_v]   1 - final transmittance */
   float* depth;  /* [sum_v H_v W_v]   median planar depth, 0 where nothing blends */
   float* normal; /* [sum_v 3 H_v W_v] blended camera-space unit normals */
+  float* dist;   /* [sum_v H_v W_v]   depth distortion L_d (Eq. 23) */
+  float* nloss;  /* [sum_v H_v W_v]   normal consistency L_n (Eq. 24) */
 } gs_maps;
 
-/* Upstream gradients dL/d(maps), same layouts as gs_maps; any may be NULL (zero). */
+/* Upstream gradients dL/d(maps), same layouts as gs_maps; any may be NULL (zero).
+ * The weights w of Eq. 23 are treated as constants (Sec. 4.1.1), so ddist
+ * reaches the parameters through the splats' planar depths only; dnloss
+ * reaches them through w, the splat normals n_i and, by the finite
+ * differences, the median depths of the pixel and its four neighbours.
+ * ddist and dnloss need params.losses = 1 and a gs_render_fwd of the same
+ * frame with it. */
 typedef struct {
   const float* dcolor;
   const float* dalpha;
   const float* ddepth;
   const float* dnormal;
+  const float* ddist;
+  const float* dnloss;
 } gs_map_grads;
 
 /* Parameter gradients of one scene (device, FP32, same shapes as gs_scene's
@@ -161,7 +189,10 @@ gs_status gs_preprocess(const gs_frame* frame, void* stream);
 gs_status gs_bin(const gs_frame* frame, void* stream);
 
 /* Front-to-back compositing (Eq. 3, Eq. 4, Sec. 1, Eq. 22) of every view into
- * `maps`; stores the per-pixel state the backward pass replays. */
+ * `maps`; stores the per-pixel state the backward pass replays.  With
+ * params.losses = 1 the same pass accumulates sum w, sum w d and sum w d^2 per
+ * pixel for Eq. 23, and a second kernel evaluates Eq. 24 when maps->nloss is
+ * set.  GS_ERR_INVALID_ARG if dist or nloss is set with params.losses = 0. */
 gs_status gs_render_fwd(const gs_frame* frame, const gs_maps* maps, void* stream);
 
 /* Backward of gs_render_fwd and of gs_preprocess: replays each pixel back to

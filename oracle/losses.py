@@ -106,7 +106,8 @@ def render_with_losses(scene, cam, upstream=None, params: RenderParams = None):
     n_splat = pre_d["n"][gidx]
     Ln = normal_consistency(r["weights"], n_splat, nt.reshape(-1, 3), ok.reshape(-1))
     maps = dict(color=r["color"], alpha=r["alpha"], depth=r["depth"], normal=r["normal"], dist=Ld,
-                nloss=Ln, margin=r["margin"], n_tilde=nt.reshape(-1, 3), n_ok=ok.reshape(-1))
+                nloss=Ln, margin=r["margin"], n_tilde=nt.reshape(-1, 3), n_ok=ok.reshape(-1),
+                weights=r["weights"], d_all=r["d_all"])
     if upstream is None:
         return {k: (v.detach().numpy() if torch.is_tensor(v) else v) for k, v in maps.items()}, None, None
     dC, dA, dD, dN, dLd, dLn = [torch.from_numpy(np.asarray(x, np.float64)) for x in upstream]

@@ -35,7 +35,7 @@ class GsView(Structure):
 class GsParams(Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("lowpass", c_float),
                 ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float),
-                ("median_T", c_float), ("clamp_margin", c_float)]
+                ("median_T", c_float), ("clamp_margin", c_float), ("losses", c_int32)]
 
 
 class GsFrame(Structure):
@@ -47,12 +47,12 @@ class GsFrame(Structure):
 
 class GsMaps(Structure):
     _fields_ = [("color", c_void_p), ("alpha", c_void_p), ("depth", c_void_p),
-                ("normal", c_void_p)]
+                ("normal", c_void_p), ("dist", c_void_p), ("nloss", c_void_p)]
 
 
 class GsMapGrads(Structure):
     _fields_ = [("dcolor", c_void_p), ("dalpha", c_void_p), ("ddepth", c_void_p),
-                ("dnormal", c_void_p)]
+                ("dnormal", c_void_p), ("ddist", c_void_p), ("dnloss", c_void_p)]
 
 
 class GsSceneGrads(Structure):

@@ -65,6 +65,7 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
     return fail(GS_ERR_INVALID_ARG, "median_T must be in (0, 1)");
   if (!(p.clamp_margin >= 0.f) || !std::isfinite(p.clamp_margin))
     return fail(GS_ERR_INVALID_ARG, "clamp_margin must be finite and >= 0");
+  if (p.losses != 0 && p.losses != 1) return fail(GS_ERR_INVALID_ARG, "losses must be 0 or 1");
   if (f->pair_capacity < 1 || f->pair_capacity > (int64_t(1) << 31) - 1)
     return fail(GS_ERR_INVALID_ARG, "pair_capacity must be in [1, 2^31 - 1]");
 
@@ -142,6 +143,7 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   fd.lowpass = p.lowpass; fd.alpha_min = p.alpha_min; fd.alpha_max = p.alpha_max;
   fd.T_min = p.T_min; fd.median_T = p.median_T;
   fd.ext_c = (float)(2.0 * std::log(1.0 / (double)p.alpha_min));
+  fd.losses = p.losses;
 
   // ---- workspace layout ----
   memset(&L, 0, sizeof(L));
@@ -171,6 +173,7 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   L.px_last = take(4 * (size_t)NPIX);
   L.px_med = take(4 * (size_t)NPIX);
   L.grad2d = take(64 * (size_t)E);
+  L.px_loss = take(p.losses ? 4 * (size_t)kLossPlanes * NPIX : 0);
   L.total = off;
   return GS_OK;
 }
@@ -252,8 +255,15 @@ gs_status gs_render_fwd(const gs_frame* frame, const gs_maps* maps, void* stream
   gs_status st = prepare_ws(frame, fd, L);
   if (st != GS_OK) return st;
   if (!maps) return fail(GS_ERR_INVALID_ARG, "maps is NULL");
-  cudaError_t e = launch_render_fwd(frame->workspace, L, fd, *maps, static_cast<cudaStream_t>(stream));
+  if (!fd.losses && (maps->dist || maps->nloss))
+    return fail(GS_ERR_INVALID_ARG, "the dist and nloss maps need params.losses = 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_render_fwd(frame->workspace, L, fd, *maps, s);
   if (e != cudaSuccess) return cuda_fail(e, "render_fwd");
+  if (maps->nloss) {
+    e = launch_nloss_fwd(frame->workspace, L, fd, maps->nloss, s);
+    if (e != cudaSuccess) return cuda_fail(e, "nloss_fwd");
+  }
   return GS_OK;
 }
 
@@ -263,7 +273,15 @@ gs_status gs_composite_bwd(const gs_frame* frame, const gs_map_grads* dmaps, voi
   gs_status st = prepare_ws(frame, fd, L);
   if (st != GS_OK) return st;
   if (!dmaps) return fail(GS_ERR_INVALID_ARG, "dmaps must not be NULL");
-  cudaError_t e = launch_render_bwd(frame->workspace, L, fd, *dmaps, static_cast<cudaStream_t>(stream));
+  if (!fd.losses && (dmaps->ddist || dmaps->dnloss))
+    return fail(GS_ERR_INVALID_ARG, "ddist and dnloss need params.losses = 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (dmaps->dnloss) {
+    e = launch_nloss_bwd(frame->workspace, L, fd, dmaps->dnloss, s);
+    if (e != cudaSuccess) return cuda_fail(e, "nloss_bwd");
+  }
+  e = launch_render_bwd(frame->workspace, L, fd, *dmaps, s);
   if (e != cudaSuccess) return cuda_fail(e, "composite_bwd");
   return GS_OK;
 }

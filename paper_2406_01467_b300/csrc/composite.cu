@@ -17,11 +17,21 @@
 // splat skipped this way is one every pixel of the block would have skipped by
 // the alpha test, so the maps are the same as without the culling.
 //
+// With the loss state on (LOSS), the forward also accumulates, per pixel, the
+// shifted moments S1 = sum w (d - d0), S2 = sum w (d - d0)^2 of the splats'
+// planar depths d (d0 = the first contributor's depth), which give the depth
+// distortion of Eq. 23 as 2 (W S2 - S1^2), W = sum w, in one pass: the double
+// sum over pairs expands to that, and the shift leaves it unchanged while
+// keeping the FP32 cancellation small.
+//
 // Backward replays each pixel from its last contributor toward the front,
 // recovering T by division (alpha <= alpha_max < 1) and the colour / normal
 // "behind" sums recursively; nothing per (pixel, splat) is stored.  Each warp
 // reduces the 15 per-splat gradients of its 32 pixels with a transposed
 // reduce-scatter (16 shuffles instead of 75) and issues one vector of atomics.
+// Eq. 23 with constant weights adds dL/dd_k = 4 w_k W (d_k - mean) to each
+// contributor's planar depth; Eq. 24 enters through the map gradients of
+// alpha, normal and depth that the normal-consistency backward stored.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -121,6 +131,7 @@ __device__ inline bool reaches(const float4& f0, const float4& f1, const SubRect
 // first half and tests it against the warp's rectangle; the records that pass
 // are staged whole in the warp's shared slots and evaluated by all 32 lanes in
 // list order.  The walk ends as soon as the block's own pixels are done.
+template <bool LOSS>
 __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restrict__ ws, const Layout& L,
                                 const gs_maps& maps, int tile, int sub, float4 (*my)[4], uint32_t& evals) {
   const TileCtx c = tile_ctx(fd, tile, sub);
@@ -133,6 +144,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   const SubRect R = sub_rect(c.x0, c.y0, fd->tile_w / kSubW, sub);
 
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, depth = 0.f;
+  float Ws = 0.f, S1 = 0.f, S2 = 0.f, d0 = 0.f;   // Eq. 23 moments (LOSS only)
   int last = -1, med = -1;
   bool done = !c.inside;
   for (int c0 = range.x; c0 < range.y; c0 += 32) {
@@ -168,9 +180,17 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float4 e2 = my[j][2], e3 = my[j][3];
       C0 += w * e3.y; C1 += w * e3.z; C2 += w * e3.w;
       N0 += w * e2.z; N1 += w * e2.w; N2 += w * e3.x;
+      const float dk = b.w + e2.x * dx + e2.y * dy;   // Eq. 4
+      if (LOSS) {
+        if (last < 0) d0 = dk;
+        const float sd = dk - d0;
+        Ws += w;
+        S1 += w * sd;
+        S2 += w * sd * sd;
+      }
       if (med < 0 && Tn <= tmed) {
         med = c0 + j;
-        depth = b.w + e2.x * dx + e2.y * dy;   // Eq. 4
+        depth = dk;
       }
       last = c0 + j;
       T = Tn;
@@ -199,6 +219,16 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   at<float>(ws, L.px_T)[c.pix] = T;
   at<int>(ws, L.px_last)[c.pix] = last;
   at<int>(ws, L.px_med)[c.pix] = med;
+  if (LOSS) {
+    if (maps.dist) maps.dist[c.pix] = 2.f * (Ws * S2 - S1 * S1);
+    float* P = at<float>(ws, L.px_loss);
+    const int64_t NP = L.NPIX;
+    P[LP_MEAN * NP + c.pix] = Ws > 0.f ? d0 + S1 / Ws : 0.f;
+    P[LP_DEPTH * NP + c.pix] = depth;
+    P[LP_N0 * NP + c.pix] = N0;
+    P[(LP_N0 + 1) * NP + c.pix] = N1;
+    P[(LP_N0 + 2) * NP + c.pix] = N2;
+  }
 }
 
 // Transposed warp reduce-scatter of 16 values: afterwards lane l holds the
@@ -237,6 +267,7 @@ __device__ inline float warp_reduce_scatter16(float (&v)[16]) {
 
 // One backward work item (same decomposition as fwd_item): the warp replays
 // its pixels from their last contributors toward the front of the list.
+template <bool LOSS>
 __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restrict__ ws, const Layout& L,
                                 const gs_map_grads& g, int tile, int sub, float4 (*my)[4], uint32_t* my_e,
                                 uint32_t& evals) {
@@ -253,6 +284,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
   float Tf = 1.f;
   int last = -1, med = -1;
   float dC[3] = {0.f, 0.f, 0.f}, dN[3] = {0.f, 0.f, 0.f}, dA = 0.f, dD = 0.f;
+  float c4 = 0.f, dmean = 0.f;   // Eq. 23 (LOSS only)
   if (c.inside) {
     Tf = at<float>(ws, L.px_T)[c.pix];
     last = at<int>(ws, L.px_last)[c.pix];
@@ -268,6 +300,20 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
     }
     if (g.dalpha) dA = g.dalpha[c.pix];
     if (g.ddepth) dD = g.ddepth[c.pix];
+    if (LOSS) {
+      const float* P = at<float>(ws, L.px_loss);
+      const int64_t NP = L.NPIX;
+      if (g.dnloss) {   // Eq. 24 through the alpha, depth and normal maps
+        dA += P[LP_DA * NP + c.pix];
+        dD += P[LP_DD * NP + c.pix];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dN[k] += P[(LP_DN0 + k) * NP + c.pix];
+      }
+      if (g.ddist) {    // Eq. 23, weights constant: dL/dd_k = 4 w_k W (d_k - mean)
+        c4 = 4.f * g.ddist[c.pix] * (1.f - Tf);
+        dmean = P[LP_MEAN * NP + c.pix];
+      }
+    }
   }
   const int wmax = __reduce_max_sync(kFull, last);
 
@@ -328,7 +374,15 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
           }
           const float dal = T * dsum + dATf * ia;
           float gu = 0.f, gv = 0.f;
-          if (idx == med) {            // d = z_c + p . Delta (Eq. 4)
+          if (LOSS) {                  // d = z_c + p . Delta (Eq. 4), median and Eq. 23
+            const float dk = b.w + e2.x * dx + e2.y * dy;
+            const float sd = c4 * w * (dk - dmean) + (idx == med ? dD : 0.f);
+            gr[R_Z] = sd;
+            gr[R_P0] = sd * dx;
+            gr[R_P1] = sd * dy;
+            gu += sd * e2.x;
+            gv += sd * e2.y;
+          } else if (idx == med) {     // d = z_c + p . Delta (Eq. 4)
             gr[R_Z] = dD;
             gr[R_P0] = dD * dx;
             gr[R_P1] = dD * dy;
@@ -365,6 +419,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
 // which item (each pixel is computed by exactly one warp).
 constexpr int kRenderThreads = 256;
 
+template <bool LOSS>
 __global__ void __launch_bounds__(kRenderThreads)
 k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_maps maps, int subs,
              int n_items) {
@@ -379,12 +434,13 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     if (lane == 0) item = atomicAdd(&hdr->work_fwd, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= n_items) break;
-    fwd_item(fd, ws, L, maps, item / subs, item % subs, my, evals);
+    fwd_item<LOSS>(fd, ws, L, maps, item / subs, item % subs, my, evals);
     __syncwarp();
   }
   count_evals(evals, &hdr->n_evals_fwd);
 }
 
+template <bool LOSS>
 __global__ void __launch_bounds__(kRenderThreads)
 k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_map_grads g, int subs,
              int n_items) {
@@ -401,7 +457,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     if (lane == 0) item = atomicAdd(&hdr->work_bwd, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= n_items) break;
-    bwd_item(fd, ws, L, g, item / subs, item % subs, my, my_e, evals);
+    bwd_item<LOSS>(fd, ws, L, g, item / subs, item % subs, my, my_e, evals);
     __syncwarp();
   }
   count_evals(evals, &hdr->n_evals_bwd);
@@ -429,8 +485,12 @@ cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& hf, con
   if (L.T == 0) return cudaSuccess;
   const int subs = hf.tile_w * hf.tile_h / 32;
   const int n_items = (int)L.T * subs;
-  k_render_fwd<<<persistent_grid(k_render_fwd, n_items), kRenderThreads, 0, s>>>(fd, ws, L, maps, subs,
-                                                                                  n_items);
+  if (hf.losses)
+    k_render_fwd<true><<<persistent_grid(k_render_fwd<true>, n_items), kRenderThreads, 0, s>>>(
+        fd, ws, L, maps, subs, n_items);
+  else
+    k_render_fwd<false><<<persistent_grid(k_render_fwd<false>, n_items), kRenderThreads, 0, s>>>(
+        fd, ws, L, maps, subs, n_items);
   return cudaGetLastError();
 }
 
@@ -446,7 +506,12 @@ cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& hf, con
   if (L.T == 0) return cudaSuccess;
   const int subs = hf.tile_w * hf.tile_h / 32;
   const int n_items = (int)L.T * subs;
-  k_render_bwd<<<persistent_grid(k_render_bwd, n_items), kRenderThreads, 0, s>>>(fd, ws, L, g, subs, n_items);
+  if (hf.losses && (g.ddist || g.dnloss))
+    k_render_bwd<true><<<persistent_grid(k_render_bwd<true>, n_items), kRenderThreads, 0, s>>>(
+        fd, ws, L, g, subs, n_items);
+  else
+    k_render_bwd<false><<<persistent_grid(k_render_bwd<false>, n_items), kRenderThreads, 0, s>>>(
+        fd, ws, L, g, subs, n_items);
   return cudaGetLastError();
 }
 

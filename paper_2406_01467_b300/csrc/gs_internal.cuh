@@ -66,6 +66,19 @@ struct FrameDev {
   int32_t tile_w, tile_h, tile_shift_x, tile_shift_y;
   float lowpass, alpha_min, alpha_max, T_min, median_T;
   float ext_c;        // float32(2 ln(1/alpha_min))
+  int32_t losses;     // per-pixel state of the Eq. 23-24 losses is kept
+};
+
+// Per-pixel planes of the loss state (each [n_pixels] floats, global pixel
+// index), present when FrameDev::losses is set.
+enum LossPlane {
+  LP_MEAN = 0,             // sum w d / sum w: weighted mean planar depth (Eq. 23 backward)
+  LP_DEPTH = 1,            // copy of the median depth map
+  LP_N0 = 2,               // copy of the normal map, 3 planes
+  LP_DD = 5,               // d L_n / d depth (Eq. 24 backward)
+  LP_DN0 = 6,              // d L_n / d normal map, 3 planes
+  LP_DA = 9,               // d L_n / d alpha map
+  kLossPlanes = 10
 };
 
 // Parameter-gradient outputs, passed by value to the backward kernel.
@@ -98,6 +111,7 @@ struct Layout {
   size_t ranges;            // [T] int2
   size_t px_T, px_last, px_med;
   size_t grad2d;            // [E][16] float
+  size_t px_loss;           // [kLossPlanes][NPIX] float when losses, else 0 bytes
   size_t total;
 };
 
@@ -148,5 +162,9 @@ cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& host_fd
                               const gs_map_grads& g, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(void* ws, const Layout& L, const FrameDev& host_fd,
                                   const GradPtrs& gp, cudaStream_t s);
+cudaError_t launch_nloss_fwd(void* ws, const Layout& L, const FrameDev& host_fd, float* nloss,
+                             cudaStream_t s);
+cudaError_t launch_nloss_bwd(void* ws, const Layout& L, const FrameDev& host_fd, const float* dnloss,
+                             cudaStream_t s);
 
 }  // namespace gs

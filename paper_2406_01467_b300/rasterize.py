@@ -29,10 +29,11 @@ class RenderParams:
     T_min: float = 1e-4
     median_T: float = 0.5
     clamp_margin: float = 0.15
+    losses: bool = False      # keep the per-pixel state of Eq. 23-24 (dist / nloss maps)
 
     def to_c(self) -> GsParams:
         return GsParams(self.tile_w, self.tile_h, self.lowpass, self.alpha_min, self.alpha_max,
-                        self.T_min, self.median_T, self.clamp_margin)
+                        self.T_min, self.median_T, self.clamp_margin, int(bool(self.losses)))
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -136,7 +137,10 @@ class Frame:
         self.alpha = torch.empty(self.n_pixels, **f32)
         self.depth = torch.empty(self.n_pixels, **f32)
         self.normal = torch.empty(3 * self.n_pixels, **f32)
-        self._maps = GsMaps(_ptr(self.color), _ptr(self.alpha), _ptr(self.depth), _ptr(self.normal))
+        self.dist = torch.empty(self.n_pixels, **f32) if self.params.losses else None
+        self.nloss = torch.empty(self.n_pixels, **f32) if self.params.losses else None
+        self._maps = GsMaps(_ptr(self.color), _ptr(self.alpha), _ptr(self.depth), _ptr(self.normal),
+                            _ptr(self.dist), _ptr(self.nloss))
 
     def _bind_scenes(self):
         for i, s in enumerate(self.scenes):
@@ -205,10 +209,11 @@ class Frame:
                             sh=torch.empty(tuple(s.sh.shape), **f32)))
         return out
 
-    def backward(self, dcolor=None, dalpha=None, ddepth=None, dnormal=None, grads=None, stream=None,
-                 split: bool = False, events=None):
+    def backward(self, dcolor=None, dalpha=None, ddepth=None, dnormal=None, ddist=None, dnloss=None,
+                 grads=None, stream=None, split: bool = False, events=None):
         """Enqueue the backward pass; returns per-scene FP32 gradient dicts.
 
+        ``ddist`` / ``dnloss`` weight the Eq. 23 / Eq. 24 maps (``params.losses``).
         ``split`` issues it as gs_composite_bwd + gs_preprocess_bwd; ``events``
         (three CUDA events) are then recorded before, between and after the two."""
         def flat(t, n):
@@ -220,8 +225,9 @@ class Frame:
             return t.to(torch.float32).contiguous()
         dc, da, dd, dn = (flat(dcolor, 3 * self.n_pixels), flat(dalpha, self.n_pixels),
                           flat(ddepth, self.n_pixels), flat(dnormal, 3 * self.n_pixels))
-        self._up = (dc, da, dd, dn)   # keep alive until the stream has consumed them
-        mg = GsMapGrads(_ptr(dc), _ptr(da), _ptr(dd), _ptr(dn))
+        dl, dq = flat(ddist, self.n_pixels), flat(dnloss, self.n_pixels)
+        self._up = (dc, da, dd, dn, dl, dq)   # keep alive until the stream has consumed them
+        mg = GsMapGrads(_ptr(dc), _ptr(da), _ptr(dd), _ptr(dn), _ptr(dl), _ptr(dq))
         if grads is None:
             grads = self.alloc_grads()
         cg = (GsSceneGrads * len(self.scenes))()
@@ -253,6 +259,14 @@ class Frame:
         n = H * W
         return (self.color[3 * off:3 * (off + n)].view(3, H, W), self.alpha[off:off + n].view(H, W),
                 self.depth[off:off + n].view(H, W), self.normal[3 * off:3 * (off + n)].view(3, H, W))
+
+    def loss_maps(self, v: int = 0):
+        """(depth distortion [H,W] (Eq. 23), normal consistency [H,W] (Eq. 24)) of view v."""
+        if not self.params.losses:
+            raise ValueError("the frame was made without params.losses")
+        off = sum(h * w for h, w in self.sizes[:v])
+        H, W = self.sizes[v]
+        return self.dist[off:off + H * W].view(H, W), self.nloss[off:off + H * W].view(H, W)
 
     def debug(self):
         """Intermediate buffers (records, rects, sorted pairs, ranges, 2D gradients)."""

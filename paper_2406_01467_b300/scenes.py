@@ -270,6 +270,13 @@ def upstream_grads(rng_seed, height, width, n_views=1):
             rng.standard_normal((n_views, 3, height, width)).astype(np.float32))
 
 
+def loss_upstream(rng_seed, height, width, n_views=1):
+    """Seeded dL/d(depth distortion, normal consistency) maps, N(0,1) each, FP32."""
+    rng = np.random.Generator(np.random.PCG64(rng_seed))
+    sh = (n_views, height, width)
+    return rng.standard_normal(sh).astype(np.float32), rng.standard_normal(sh).astype(np.float32)
+
+
 def to_bf16_rounded(a: np.ndarray) -> np.ndarray:
     """Round-to-nearest-even float32 -> bfloat16, returned widened back to float32."""
     a = np.ascontiguousarray(a, np.float32)

@@ -101,3 +101,23 @@ def test_empty_scene_is_valid(lib):
     f = _frame(n=0)
     f.scenes[0] = _lib.GsScene(None, None, None, None, None, 0, 0, _lib.GS_F32)
     assert lib.gs_workspace_size(ctypes.byref(f)) > 0
+
+
+def test_loss_state_costs_ten_floats_per_pixel(lib):
+    a = lib.gs_workspace_size(ctypes.byref(_frame(100, W=64, H=48)))
+    b = lib.gs_workspace_size(ctypes.byref(_frame(100, W=64, H=48, params=RenderParams(losses=True))))
+    assert b - a >= 10 * 4 * 64 * 48 and b - a < 10 * 4 * 64 * 48 + 512
+
+
+def test_loss_maps_need_the_loss_state(lib):
+    f = _frame()
+    f.workspace = 256   # fake, aligned; the check comes before any device work
+    f.workspace_bytes = 1 << 40
+    maps = _lib.GsMaps(None, None, None, None, 256, None)
+    assert lib.gs_render_fwd(ctypes.byref(f), ctypes.byref(maps), None) == _lib.GS_ERR_INVALID_ARG
+    assert "losses" in lib.gs_last_error_string().decode()
+    mg = _lib.GsMapGrads(None, None, None, None, None, 256)
+    assert lib.gs_composite_bwd(ctypes.byref(f), ctypes.byref(mg), None) == _lib.GS_ERR_INVALID_ARG
+    assert "losses" in lib.gs_last_error_string().decode()
+    f.params.losses = 2
+    assert lib.gs_workspace_size(ctypes.byref(f)) == 0
