@@ -391,6 +391,38 @@ def run_regularized(args, device, plain_ms):
             "overhead_vs_plain_ms": round(eager - plain_ms, 4)}
 
 
+def run_geometry(args, device, n_views=48):
+    """Forward-only alpha / depth / normal render of the 3M scene from 48 views
+    (1297x840, for fusing depth into a volume), one frame, one CUDA graph; the
+    same views through the full forward (colour + backward state) for scale."""
+    import torch
+    from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, autotune, scenes
+    scene, _ = make_workload("unbounded")
+    st = SceneTensors.from_scene(scene, device)
+    views = [(c, 0) for c in scenes.fusion_cameras(n_views)]
+    out = {"workload": f"unbounded scene, 3M Gaussians, {n_views} views 1297x840 in one frame, FP32, forward only",
+           "views": n_views}
+    for name, p in (("geometry_only", RenderParams(geometry_only=True)), ("full_forward", RenderParams())):
+        fr = Frame([st], views, p)
+        fr.forward()
+        need = int(fr.stats().n_pairs)
+        fr._alloc(int(need * 1.15) + 1024)
+
+        def step(fr=fr):
+            fr.preprocess()
+            fr.bin()
+            fr.render()
+        ms, eager = timed_graph(step, max(5, args.steps // 20), args.warmup)
+        fr.stats()
+        if fr.last_status != 0:
+            raise RuntimeError(f"{name} frame status {fr.last_status}")
+        out[name] = {"ms_per_batch_graph": round(ms, 3), "ms_per_view": round(ms / n_views, 4),
+                     "workspace_gb": round(fr.frame.workspace_bytes / 1e9, 2), "pairs": need}
+        del fr, step
+        torch.cuda.empty_cache()
+    return out
+
+
 def batched_workload():
     """A 1M-Gaussian unbounded scene seen from 16 orbit views of uneven sizes,
     plus four object scenes (50K/200K/800K/2M) with one 800x600 view each."""
@@ -524,6 +556,7 @@ def main():
         out["bf16_graph"] = run_bf16(args, f"cuda:{local}")
         out["regularized"] = run_regularized(args, f"cuda:{local}", out["ms_per_step"])
         out["batched"] = run_batched(args, f"cuda:{local}")
+        out["geometry_views"] = run_geometry(args, f"cuda:{local}")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         scene, cam = make_workload(args.config)
         est, secs, cores, sample = oracle_sample(scene, cam, n_crops=64)

@@ -97,6 +97,14 @@ typedef struct {
                              of Eq. 23-24 and their backward need (10 floats per pixel
                              of workspace); with 0, gs_maps.dist / nloss and
                              gs_map_grads.ddist / dnloss must be NULL */
+  int32_t geometry_only;  /* 0 or 1.  1 renders alpha, depth and normal only, for
+                             fusing many views into a volume: the SH coefficients are
+                             not read (so non-finite SH do not cull), no colour is
+                             blended (gs_maps.color must be NULL), and no per-pixel
+                             backward state or 2D-gradient buffer is kept, so the
+                             workspace shrinks by 12 B per pixel and 64 B per entry and
+                             the backward calls return GS_ERR_INVALID_ARG.  Excludes
+                             losses = 1. */
 } gs_params;
 
 /* Everything a call needs to know about one frame (a batch of views). */

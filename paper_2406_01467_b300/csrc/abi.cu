@@ -66,6 +66,10 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   if (!(p.clamp_margin >= 0.f) || !std::isfinite(p.clamp_margin))
     return fail(GS_ERR_INVALID_ARG, "clamp_margin must be finite and >= 0");
   if (p.losses != 0 && p.losses != 1) return fail(GS_ERR_INVALID_ARG, "losses must be 0 or 1");
+  if (p.geometry_only != 0 && p.geometry_only != 1)
+    return fail(GS_ERR_INVALID_ARG, "geometry_only must be 0 or 1");
+  if (p.geometry_only && p.losses)
+    return fail(GS_ERR_INVALID_ARG, "geometry_only excludes losses (no backward state)");
   if (f->pair_capacity < 1 || f->pair_capacity > (int64_t(1) << 31) - 1)
     return fail(GS_ERR_INVALID_ARG, "pair_capacity must be in [1, 2^31 - 1]");
 
@@ -144,6 +148,7 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   fd.T_min = p.T_min; fd.median_T = p.median_T;
   fd.ext_c = (float)(2.0 * std::log(1.0 / (double)p.alpha_min));
   fd.losses = p.losses;
+  fd.geometry_only = p.geometry_only;
 
   // ---- workspace layout ----
   memset(&L, 0, sizeof(L));
@@ -169,10 +174,11 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   L.hist = take(4 * (size_t)kRadix * nbmax);
   L.htot = take(4 * (size_t)kRadix);
   L.ranges = take(8 * (size_t)T);
-  L.px_T = take(4 * (size_t)NPIX);
-  L.px_last = take(4 * (size_t)NPIX);
-  L.px_med = take(4 * (size_t)NPIX);
-  L.grad2d = take(64 * (size_t)E);
+  const bool bwd_state = !p.geometry_only;   // per-pixel replay state and 2D gradients
+  L.px_T = take(bwd_state ? 4 * (size_t)NPIX : 0);
+  L.px_last = take(bwd_state ? 4 * (size_t)NPIX : 0);
+  L.px_med = take(bwd_state ? 4 * (size_t)NPIX : 0);
+  L.grad2d = take(bwd_state ? 64 * (size_t)E : 0);
   L.px_loss = take(p.losses ? 4 * (size_t)kLossPlanes * NPIX : 0);
   L.total = off;
   return GS_OK;
@@ -257,6 +263,8 @@ gs_status gs_render_fwd(const gs_frame* frame, const gs_maps* maps, void* stream
   if (!maps) return fail(GS_ERR_INVALID_ARG, "maps is NULL");
   if (!fd.losses && (maps->dist || maps->nloss))
     return fail(GS_ERR_INVALID_ARG, "the dist and nloss maps need params.losses = 1");
+  if (fd.geometry_only && maps->color)
+    return fail(GS_ERR_INVALID_ARG, "geometry_only renders no colour: maps->color must be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = launch_render_fwd(frame->workspace, L, fd, *maps, s);
   if (e != cudaSuccess) return cuda_fail(e, "render_fwd");
@@ -273,6 +281,7 @@ gs_status gs_composite_bwd(const gs_frame* frame, const gs_map_grads* dmaps, voi
   gs_status st = prepare_ws(frame, fd, L);
   if (st != GS_OK) return st;
   if (!dmaps) return fail(GS_ERR_INVALID_ARG, "dmaps must not be NULL");
+  if (fd.geometry_only) return fail(GS_ERR_INVALID_ARG, "geometry_only frames have no backward");
   if (!fd.losses && (dmaps->ddist || dmaps->dnloss))
     return fail(GS_ERR_INVALID_ARG, "ddist and dnloss need params.losses = 1");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -292,6 +301,7 @@ gs_status gs_preprocess_bwd(const gs_frame* frame, const gs_scene_grads* grads, 
   gs_status st = prepare_ws(frame, fd, L);
   if (st != GS_OK) return st;
   if (!grads) return fail(GS_ERR_INVALID_ARG, "grads must not be NULL");
+  if (fd.geometry_only) return fail(GS_ERR_INVALID_ARG, "geometry_only frames have no backward");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   GradPtrs gp;
   memset(&gp, 0, sizeof(gp));
@@ -329,6 +339,8 @@ gs_status gs_debug_copy(const gs_frame* frame, float* rec, int32_t* rect, int32_
   Layout L;
   gs_status st = prepare_ws(frame, fd, L);
   if (st != GS_OK) return st;
+  if (fd.geometry_only && grad2d)
+    return fail(GS_ERR_INVALID_ARG, "geometry_only frames keep no 2D gradients");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void* ws = frame->workspace;
   cudaError_t e = cudaSuccess;

@@ -131,7 +131,7 @@ __device__ inline bool reaches(const float4& f0, const float4& f1, const SubRect
 // first half and tests it against the warp's rectangle; the records that pass
 // are staged whole in the warp's shared slots and evaluated by all 32 lanes in
 // list order.  The walk ends as soon as the block's own pixels are done.
-template <bool LOSS>
+template <bool LOSS, bool GEO>
 __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restrict__ ws, const Layout& L,
                                 const gs_maps& maps, int tile, int sub, float4 (*my)[4], uint32_t& evals) {
   const TileCtx c = tile_ctx(fd, tile, sub);
@@ -178,7 +178,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       if (Tn < tmin) { done = true; continue; }
       const float w = al * T;
       const float4 e2 = my[j][2], e3 = my[j][3];
-      C0 += w * e3.y; C1 += w * e3.z; C2 += w * e3.w;
+      if (!GEO) { C0 += w * e3.y; C1 += w * e3.z; C2 += w * e3.w; }
       N0 += w * e2.z; N1 += w * e2.w; N2 += w * e3.x;
       const float dk = b.w + e2.x * dx + e2.y * dy;   // Eq. 4
       if (LOSS) {
@@ -206,7 +206,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   }
   const int64_t HW = (int64_t)c.W * c.H;
   const int64_t p = c.pix_local;
-  if (maps.color) {
+  if (!GEO && maps.color) {
     float* col = maps.color + 3 * c.pix_base;
     col[p] = C0; col[HW + p] = C1; col[2 * HW + p] = C2;
   }
@@ -216,6 +216,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   }
   if (maps.alpha) maps.alpha[c.pix] = 1.f - T;
   if (maps.depth) maps.depth[c.pix] = depth;
+  if (GEO) return;   // forward-only geometry: no backward state
   at<float>(ws, L.px_T)[c.pix] = T;
   at<int>(ws, L.px_last)[c.pix] = last;
   at<int>(ws, L.px_med)[c.pix] = med;
@@ -419,7 +420,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
 // which item (each pixel is computed by exactly one warp).
 constexpr int kRenderThreads = 256;
 
-template <bool LOSS>
+template <bool LOSS, bool GEO>
 __global__ void __launch_bounds__(kRenderThreads)
 k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_maps maps, int subs,
              int n_items) {
@@ -434,7 +435,7 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     if (lane == 0) item = atomicAdd(&hdr->work_fwd, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= n_items) break;
-    fwd_item<LOSS>(fd, ws, L, maps, item / subs, item % subs, my, evals);
+    fwd_item<LOSS, GEO>(fd, ws, L, maps, item / subs, item % subs, my, evals);
     __syncwarp();
   }
   count_evals(evals, &hdr->n_evals_fwd);
@@ -485,12 +486,15 @@ cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& hf, con
   if (L.T == 0) return cudaSuccess;
   const int subs = hf.tile_w * hf.tile_h / 32;
   const int n_items = (int)L.T * subs;
-  if (hf.losses)
-    k_render_fwd<true><<<persistent_grid(k_render_fwd<true>, n_items), kRenderThreads, 0, s>>>(
+  if (hf.geometry_only)
+    k_render_fwd<false, true><<<persistent_grid(k_render_fwd<false, true>, n_items), kRenderThreads, 0, s>>>(
+        fd, ws, L, maps, subs, n_items);
+  else if (hf.losses)
+    k_render_fwd<true, false><<<persistent_grid(k_render_fwd<true, false>, n_items), kRenderThreads, 0, s>>>(
         fd, ws, L, maps, subs, n_items);
   else
-    k_render_fwd<false><<<persistent_grid(k_render_fwd<false>, n_items), kRenderThreads, 0, s>>>(
-        fd, ws, L, maps, subs, n_items);
+    k_render_fwd<false, false><<<persistent_grid(k_render_fwd<false, false>, n_items), kRenderThreads, 0,
+                                 s>>>(fd, ws, L, maps, subs, n_items);
   return cudaGetLastError();
 }
 

@@ -67,6 +67,8 @@ struct FrameDev {
   float lowpass, alpha_min, alpha_max, T_min, median_T;
   float ext_c;        // float32(2 ln(1/alpha_min))
   int32_t losses;     // per-pixel state of the Eq. 23-24 losses is kept
+  int32_t geometry_only;  // forward-only alpha / depth / normal, no backward state
+  int32_t pad_;
 };
 
 // Per-pixel planes of the loss state (each [n_pixels] floats, global pixel

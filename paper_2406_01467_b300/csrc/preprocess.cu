@@ -255,7 +255,9 @@ __device__ inline void load_sh(const SceneDev& S, int64_t g, float* c) {
 // ---------------------------------------------------------------------------
 // Forward
 // ---------------------------------------------------------------------------
-template <typename T, int D>
+// GEO: forward-only geometry (alpha, depth, normal); SH coefficients are not
+// read and the colour is left 0.  One launch covers every SH degree.
+template <typename T, int D, bool GEO>
 __global__ void __launch_bounds__(kPreThreads)
 k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
   constexpr int K = (D + 1) * (D + 1);
@@ -271,7 +273,7 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
     const Chunk ch = chunk_of(fd, bi);
     const ViewDev& V = fd->views[ch.view];
     const SceneDev& S = fd->scenes[V.scene];
-    if (S.dtype != dtype_code<T>() || S.sh_degree != D) continue;
+    if (S.dtype != dtype_code<T>() || (!GEO && S.sh_degree != D)) continue;
     const int t = threadIdx.x;
     if (t >= ch.n) continue;
     const int64_t e = ch.e0 + t, g = ch.g0 + t;
@@ -359,11 +361,13 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
     if (valid) {
       // SH coefficients are read only for entries that survive the culling
       float c[3 * K];
-      load_sh<T, K>(S, g, c);
-      float shchk = 0.f;
+      if constexpr (!GEO) {
+        load_sh<T, K>(S, g, c);
+        float shchk = 0.f;
 #pragma unroll
-      for (int j = 0; j < 3 * K; ++j) shchk += c[j] * 0.f;
-      if (shchk != 0.f) { valid = false; ++nonfinite; }
+        for (int j = 0; j < 3 * K; ++j) shchk += c[j] * 0.f;
+        if (shchk != 0.f) { valid = false; ++nonfinite; }
+      }
       const float tc = sqrtf(xc[0] * xc[0] + xc[1] * xc[1] + xc[2] * xc[2]);
       const float it = 1.f / tc;
       const float J2[3] = {xc[0] * it, xc[1] * it, xc[2] * it};   // third row of J: d|x|/dx
@@ -394,16 +398,18 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
       nn[0] = mv0 * im; nn[1] = mv1 * im; nn[2] = mv2 * im;
       valid = valid && (det > 0.f) && isfinite(conic[0]) && isfinite(conic[1]) && isfinite(conic[2]) &&
               isfinite(pp[0]) && isfinite(pp[1]) && isfinite(nn[0]) && isfinite(nn[1]) && isfinite(nn[2]);
-      float d[3] = {m[0] - V.campos[0], m[1] - V.campos[1], m[2] - V.campos[2]};
-      float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-      float Y[16];
-      sh_basis(d[0] * il, d[1] * il, d[2] * il, Y);
+      if constexpr (!GEO) {
+        float d[3] = {m[0] - V.campos[0], m[1] - V.campos[1], m[2] - V.campos[2]};
+        float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        float Y[16];
+        sh_basis(d[0] * il, d[1] * il, d[2] * il, Y);
 #pragma unroll
-      for (int ch3 = 0; ch3 < 3; ++ch3) {
-        float acc = 0.5f;
+        for (int ch3 = 0; ch3 < 3; ++ch3) {
+          float acc = 0.5f;
 #pragma unroll
-        for (int j = 0; j < K; ++j) acc += Y[j] * c[3 * j + ch3];
-        rgb[ch3] = fmaxf(acc, 0.f);
+          for (int j = 0; j < K; ++j) acc += Y[j] * c[3 * j + ch3];
+          rgb[ch3] = fmaxf(acc, 0.f);
+        }
       }
     }
     if (valid) {
@@ -641,10 +647,10 @@ static int grid_chunks(int n_chunks) {
 template <typename T>
 static cudaError_t fwd_t(int deg, const FrameDev* fd, void* ws, const Layout& L, int grid, cudaStream_t s) {
   switch (deg) {
-    case 0: k_preprocess<T, 0><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
-    case 1: k_preprocess<T, 1><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
-    case 2: k_preprocess<T, 2><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
-    default: k_preprocess<T, 3><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
+    case 0: k_preprocess<T, 0, false><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
+    case 1: k_preprocess<T, 1, false><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
+    case 2: k_preprocess<T, 2, false><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
+    default: k_preprocess<T, 3, false><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
   }
   return cudaGetLastError();
 }
@@ -676,6 +682,11 @@ cudaError_t launch_preprocess(void* ws, const Layout& L, const FrameDev& hf, cud
   const unsigned k = kinds(hf);
   const int grid = grid_chunks(hf.n_chunks);
   cudaError_t e = cudaSuccess;
+  if (hf.geometry_only) {   // one launch per dtype, SH not read
+    if (k & (0xFu << (4 * GS_F32))) k_preprocess<float, 0, true><<<grid, kPreThreads, 0, s>>>(fd, ws, L);
+    if (k & (0xFu << (4 * GS_BF16))) k_preprocess<__nv_bfloat16, 0, true><<<grid, kPreThreads, 0, s>>>(fd, ws, L);
+    return cudaGetLastError();
+  }
   for (int deg = 0; deg < 4 && e == cudaSuccess; ++deg) {
     if (k & (1u << (4 * GS_F32 + deg))) e = fwd_t<float>(deg, fd, ws, L, grid, s);
     if (e == cudaSuccess && (k & (1u << (4 * GS_BF16 + deg)))) e = fwd_t<__nv_bfloat16>(deg, fd, ws, L, grid, s);

@@ -30,10 +30,12 @@ class RenderParams:
     median_T: float = 0.5
     clamp_margin: float = 0.15
     losses: bool = False      # keep the per-pixel state of Eq. 23-24 (dist / nloss maps)
+    geometry_only: bool = False   # forward-only alpha / depth / normal (no colour, no backward)
 
     def to_c(self) -> GsParams:
         return GsParams(self.tile_w, self.tile_h, self.lowpass, self.alpha_min, self.alpha_max,
-                        self.T_min, self.median_T, self.clamp_margin, int(bool(self.losses)))
+                        self.T_min, self.median_T, self.clamp_margin, int(bool(self.losses)),
+                        int(bool(self.geometry_only)))
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -133,7 +135,7 @@ class Frame:
         cap = pair_capacity if pair_capacity is not None else max(1 << 16, 8 * self.n_entries)
         self._alloc(cap)
         f32 = dict(device=self.device, dtype=torch.float32)
-        self.color = torch.empty(3 * self.n_pixels, **f32)
+        self.color = None if self.params.geometry_only else torch.empty(3 * self.n_pixels, **f32)
         self.alpha = torch.empty(self.n_pixels, **f32)
         self.depth = torch.empty(self.n_pixels, **f32)
         self.normal = torch.empty(3 * self.n_pixels, **f32)
@@ -253,11 +255,13 @@ class Frame:
 
     # ------------------------------------------------------------------
     def view_maps(self, v: int = 0):
-        """(colour [3,H,W], alpha [H,W], depth [H,W], normal [3,H,W]) of view v."""
+        """(colour [3,H,W], alpha [H,W], depth [H,W], normal [3,H,W]) of view v
+        (colour None for a geometry-only frame)."""
         off = sum(h * w for h, w in self.sizes[:v])
         H, W = self.sizes[v]
         n = H * W
-        return (self.color[3 * off:3 * (off + n)].view(3, H, W), self.alpha[off:off + n].view(H, W),
+        col = None if self.color is None else self.color[3 * off:3 * (off + n)].view(3, H, W)
+        return (col, self.alpha[off:off + n].view(H, W),
                 self.depth[off:off + n].view(H, W), self.normal[3 * off:3 * (off + n)].view(3, H, W))
 
     def loss_maps(self, v: int = 0):
@@ -279,7 +283,7 @@ class Frame:
         pt = torch.zeros(P, dtype=torch.int32, device=dev)
         pe = torch.zeros(P, dtype=torch.int32, device=dev)
         rg = torch.zeros((T, 2), dtype=torch.int32, device=dev)
-        g2 = torch.zeros((E, 16), dtype=torch.float32, device=dev)
+        g2 = None if self.params.geometry_only else torch.zeros((E, 16), dtype=torch.float32, device=dev)
         check(self.lib.gs_debug_copy(ctypes.byref(self.frame), _ptr(rec), _ptr(rect), _ptr(pt), _ptr(pe),
                                      _ptr(rg), _ptr(g2), _stream(None)), "gs_debug_copy")
         st = self.stats()

@@ -260,6 +260,21 @@ def orbit_cameras(n_views=16, seed=3, radius=7.0):
     return cams
 
 
+def fusion_cameras(n_views=48, seed=6, radius=7.0, width=1297, height=840):
+    """Views for fusing depth into a volume: yaw k*360/n on a radius-7 orbit,
+    elevation ~ U[-0.3, 0.3] rad, all W x H with f = 1150 W / 1297, looking at
+    the origin."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    el = rng.uniform(-0.3, 0.3, n_views)
+    f = 1150.0 * width / 1297.0
+    cams = []
+    for k in range(n_views):
+        a = 2.0 * np.pi * k / n_views
+        eye = (radius * np.cos(el[k]) * np.sin(a), radius * np.sin(el[k]), -radius * np.cos(el[k]) * np.cos(a))
+        cams.append(Camera(look_at(eye, (0.0, 0.0, 0.0)), f, f, width / 2.0, height / 2.0, width, height))
+    return cams
+
+
 def upstream_grads(rng_seed, height, width, n_views=1):
     """Seeded dL/d(colour, alpha, depth, normal) maps, N(0,1) each, FP32."""
     rng = np.random.Generator(np.random.PCG64(rng_seed))

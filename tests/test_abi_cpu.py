@@ -121,3 +121,23 @@ def test_loss_maps_need_the_loss_state(lib):
     assert "losses" in lib.gs_last_error_string().decode()
     f.params.losses = 2
     assert lib.gs_workspace_size(ctypes.byref(f)) == 0
+
+
+def test_geometry_only_drops_the_backward_state(lib):
+    a = lib.gs_workspace_size(ctypes.byref(_frame(1000, W=64, H=48)))
+    b = lib.gs_workspace_size(ctypes.byref(_frame(1000, W=64, H=48, params=RenderParams(geometry_only=True))))
+    assert a - b >= 12 * 64 * 48 + 64 * 1000
+    f = _frame(params=RenderParams(geometry_only=True))
+    f.workspace = 256
+    f.workspace_bytes = 1 << 40
+    maps = _lib.GsMaps(256, None, None, None, None, None)
+    assert lib.gs_render_fwd(ctypes.byref(f), ctypes.byref(maps), None) == _lib.GS_ERR_INVALID_ARG
+    assert "colour" in lib.gs_last_error_string().decode()
+    mg = _lib.GsMapGrads(None, None, None, None, None, None)
+    assert lib.gs_composite_bwd(ctypes.byref(f), ctypes.byref(mg), None) == _lib.GS_ERR_INVALID_ARG
+    sg = (_lib.GsSceneGrads * 1)()
+    assert lib.gs_preprocess_bwd(ctypes.byref(f), sg, None) == _lib.GS_ERR_INVALID_ARG
+    assert lib.gs_render_bwd(ctypes.byref(f), ctypes.byref(mg), sg, None) == _lib.GS_ERR_INVALID_ARG
+    assert "no backward" in lib.gs_last_error_string().decode()
+    f.params.losses = 1
+    assert lib.gs_workspace_size(ctypes.byref(f)) == 0
