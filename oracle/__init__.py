@@ -23,5 +23,5 @@ mathematics fixes (closed forms, library routines, invariants, brute force,
 finite differences) by the ``-m "not gpu"`` tests.
 """
 from .params import RenderParams  # noqa: F401
-from . import sh, gaussians, binning, composite, losses  # noqa: F401
+from . import sh, gaussians, binning, composite, losses, filter3d  # noqa: F401
 from .render import render, render_grads  # noqa: F401

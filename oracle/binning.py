@@ -28,17 +28,22 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import filter3d
 from .params import RenderParams, clamp_limits_f32
 
 F = np.float32
 
 
-def decide(means, scales, quats, opacities, cam, params: RenderParams):
-    """Per-Gaussian FP32 decisions: validity, depth key, pixel and tile rectangles."""
+def decide(means, scales, quats, opacities, cam, params: RenderParams, filter_var=None):
+    """Per-Gaussian FP32 decisions: validity, depth key, pixel and tile rectangles.
+    With ``filter_var`` the Mip-Splatting 3D filter is applied first (FP32 chain
+    of ``filter3d.apply_filter_f32``)."""
     m = np.asarray(means, F)
     s = np.asarray(scales, F)
     qq = np.asarray(quats, F)
     o = np.asarray(opacities, F)
+    if filter_var is not None:
+        s, o = filter3d.apply_filter_f32(s, o, filter_var)
     V = np.asarray(cam.viewmat, F)
     fx, fy, cx, cy = F(cam.fx), F(cam.fy), F(cam.cx), F(cam.cy)
     W, H = int(cam.width), int(cam.height)
@@ -148,3 +153,9 @@ def tile_lists(dec, cam, params: RenderParams, brute_force: bool = False):
         last = np.searchsorted(tile, np.arange(T), side="right")
         ranges[:, 0], ranges[:, 1] = first, last
     return tile, g, ranges
+
+
+def decide_scene(scene, cam, params: RenderParams):
+    """``decide`` for a scene object (its 3D filter variances, if any, included)."""
+    return decide(scene.means, scene.scales, scene.quats, scene.opacities, cam, params,
+                  getattr(scene, "filter_var", None))

@@ -92,7 +92,7 @@ def render_with_losses(scene, cam, upstream=None, params: RenderParams = None):
     without ``upstream``.  Small images only (one dense autograd graph)."""
     params = params or RenderParams()
     H, W = cam.height, cam.width
-    dec = binning.decide(scene.means, scene.scales, scene.quats, scene.opacities, cam, params)
+    dec = binning.decide_scene(scene, cam, params)
     leaves = _leaves(scene, upstream is not None)
     pre = _project(leaves, scene, cam, params)
     pre_d = {k: pre[k].detach().clone().requires_grad_(upstream is not None) for k in PRE2D}

@@ -4,7 +4,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import binning, composite as comp, gaussians
+from . import binning, composite as comp, filter3d, gaussians
 from .params import RenderParams
 
 DT = torch.float64
@@ -22,9 +22,13 @@ def _leaves(scene, requires_grad):
 
 
 def _project(leaves, scene, cam, params, route="schur"):
-    return gaussians.project(leaves["means"], leaves["scales"], leaves["quats"],
-                             leaves["opacities"], leaves["sh"], scene.sh_degree, cam, params,
-                             route=route)
+    scales, opacities = leaves["scales"], leaves["opacities"]
+    fv = getattr(scene, "filter_var", None)
+    if fv is not None:   # Mip-Splatting 3D filter (Sec. 4.1.1)
+        scales, opacities = filter3d.apply_filter(scales, opacities,
+                                                  torch.tensor(np.asarray(fv, np.float64), dtype=DT))
+    return gaussians.project(leaves["means"], scales, leaves["quats"], opacities, leaves["sh"],
+                             scene.sh_degree, cam, params, route=route)
 
 
 def _chunks(pixels, size):
@@ -38,7 +42,7 @@ def render(scene, cam, params: RenderParams = None, pixels=None, chunk=4096, rou
     Returns a dict of numpy arrays: color (P,3), alpha, depth, normal (P,3),
     margin, n_contrib, pixels, plus the FP32 binning decisions ``dec``."""
     params = params or RenderParams()
-    dec = binning.decide(scene.means, scene.scales, scene.quats, scene.opacities, cam, params)
+    dec = binning.decide_scene(scene, cam, params)
     with torch.no_grad():
         pre = _project(_leaves(scene, False), scene, cam, params, route)
         if pixels is None:
@@ -74,7 +78,7 @@ def render_grads(scene, cam, upstream, params: RenderParams = None, pixels=None,
     dN = dN.reshape(3, H_ * W_)
     dA = dA.reshape(H_ * W_)
     dD = dD.reshape(H_ * W_)
-    dec = binning.decide(scene.means, scene.scales, scene.quats, scene.opacities, cam, params)
+    dec = binning.decide_scene(scene, cam, params)
     leaves = _leaves(scene, True)
     pre = _project(leaves, scene, cam, params, route)
     # detached copies of the 2D quantities: the composite is differentiated

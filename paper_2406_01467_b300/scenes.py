@@ -19,6 +19,7 @@ written in each function, then cast to float32.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
+from typing import Optional
 
 import numpy as np
 from scipy.spatial.transform import Rotation
@@ -54,14 +55,16 @@ class Scene:
     sh_degree: int
     name: str = ""
     meta: dict = field(default_factory=dict)
+    filter_var: Optional[np.ndarray] = None   # (N,) float32 3D-filter variances, or None
 
     @property
     def n(self) -> int:
         return int(self.means.shape[0])
 
     def subset(self, idx) -> "Scene":
+        fv = None if self.filter_var is None else self.filter_var[idx]
         return Scene(self.means[idx], self.scales[idx], self.quats[idx], self.opacities[idx],
-                     self.sh[idx], self.sh_degree, self.name + "[subset]", dict(self.meta))
+                     self.sh[idx], self.sh_degree, self.name + "[subset]", dict(self.meta), fv)
 
 
 def look_at(eye, target, down=(0.0, 1.0, 0.0)) -> np.ndarray:
