@@ -72,6 +72,12 @@ typedef struct {
   int64_t n;             /* number of Gaussians, >= 0 */
   int32_t sh_degree;     /* 0..3 */
   int32_t dtype;         /* gs_dtype of every array above */
+  const float* filter_var; /* [n] FP32 (whatever dtype is) Mip-Splatting 3D filter
+                              variances v >= 0, or NULL for no filter (Sec. 4.1.1):
+                              the covariance becomes Sigma + v I, i.e. every scale
+                              s -> sqrt(s^2 + v), and the opacity is multiplied by
+                              prod s / sqrt(s^2 + v) (the integral of o G is kept).
+                              Gradients flow to the unfiltered scales and opacity. */
 } gs_scene;
 
 /* One camera (Sec. 3.1: W is the world->camera rotation). */
@@ -219,6 +225,15 @@ gs_status gs_composite_bwd(const gs_frame* frame, const gs_map_grads* dmaps, voi
  * 8-22 and the SH colour) from the workspace's per-entry gradients to the
  * parameters.  Buffers of scenes seen by several views are zeroed, then summed. */
 gs_status gs_preprocess_bwd(const gs_frame* frame, const gs_scene_grads* grads, void* stream);
+
+/* Mip-Splatting 3D filter variances of scene `scene` from the frame's views of
+ * it (Sec. 4.1.1): v = scale * min_n (z_n / fx_n)^2 over the views n in which
+ * the Gaussian's centre has camera z > near_plane and projects inside the image
+ * widened by 15 % of its size on each side; a Gaussian seen by no view gets the
+ * largest v of the seen ones (0 if none is seen).  `filter_var` is device FP32
+ * [n]; Mip-Splatting's scale is 0.2.  Runs on `stream` and resets the
+ * workspace's counters and status like gs_preprocess. */
+gs_status gs_filter3d(const gs_frame* frame, int32_t scene, float scale, float* filter_var, void* stream);
 
 /* Intermediate results for tests and tools, copied to caller device buffers on
  * `stream`; any pointer may be NULL.  rec: [n_entries][16] FP32 per-entry

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "G
 class GsScene(Structure):
     _fields_ = [("means", c_void_p), ("scales", c_void_p), ("quats", c_void_p),
                 ("opacities", c_void_p), ("sh", c_void_p), ("n", c_int64),
-                ("sh_degree", c_int32), ("dtype", c_int32)]
+                ("sh_degree", c_int32), ("dtype", c_int32), ("filter_var", c_void_p)]
 
 
 class GsView(Structure):
@@ -68,7 +68,7 @@ class GsStats(Structure):
 
 
 EXPORTS = ("gs_workspace_size", "gs_preprocess", "gs_bin", "gs_render_fwd", "gs_render_bwd",
-           "gs_composite_bwd", "gs_preprocess_bwd", "gs_debug_copy", "gs_render_fwd_static",
+           "gs_composite_bwd", "gs_preprocess_bwd", "gs_filter3d", "gs_debug_copy", "gs_render_fwd_static",
            "gs_check", "gs_last_error_string")
 STATIC_SCRATCH_BYTES = 32 << 20
 
@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH):
     lib.gs_composite_bwd.restype = c_int32
     lib.gs_preprocess_bwd.argtypes = [pf, POINTER(GsSceneGrads), c_void_p]
     lib.gs_preprocess_bwd.restype = c_int32
+    lib.gs_filter3d.argtypes = [pf, c_int32, c_float, c_void_p, c_void_p]
+    lib.gs_filter3d.restype = c_int32
     lib.gs_debug_copy.argtypes = [pf, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p]
     lib.gs_debug_copy.restype = c_int32

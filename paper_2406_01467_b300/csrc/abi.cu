@@ -85,6 +85,7 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
       return fail(GS_ERR_INVALID_ARG, "scene %d: NULL parameter array", i);
     SceneDev& d = fd.scenes[i];
     d.means = s.means; d.scales = s.scales; d.quats = s.quats; d.opacities = s.opacities; d.sh = s.sh;
+    d.filter_var = static_cast<const float*>(s.filter_var);
     d.n = s.n; d.sh_degree = s.sh_degree; d.dtype = s.dtype;
   }
   int64_t E = 0, NPIX = 0;
@@ -331,6 +332,21 @@ gs_status gs_render_bwd(const gs_frame* frame, const gs_map_grads* dmaps, const 
   gs_status st = gs_composite_bwd(frame, dmaps, stream);
   if (st != GS_OK) return st;
   return gs_preprocess_bwd(frame, grads, stream);
+}
+
+gs_status gs_filter3d(const gs_frame* frame, int32_t scene, float scale, float* filter_var, void* stream) {
+  FrameDev fd;
+  Layout L;
+  gs_status st = prepare_ws(frame, fd, L);
+  if (st != GS_OK) return st;
+  if (scene < 0 || scene >= frame->n_scenes) return fail(GS_ERR_INVALID_ARG, "scene index %d out of range", scene);
+  if (!(scale >= 0.f) || !std::isfinite(scale)) return fail(GS_ERR_INVALID_ARG, "scale must be finite and >= 0");
+  if (frame->scenes[scene].n > 0 && !filter_var) return fail(GS_ERR_INVALID_ARG, "filter_var is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_setup(fd, frame->workspace, L, s);
+  if (e == cudaSuccess) e = launch_filter3d(frame->workspace, L, fd, scene, scale, filter_var, s);
+  if (e != cudaSuccess) return cuda_fail(e, "filter3d");
+  return GS_OK;
 }
 
 gs_status gs_debug_copy(const gs_frame* frame, float* rec, int32_t* rect, int32_t* pair_tile,

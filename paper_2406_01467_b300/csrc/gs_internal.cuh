@@ -51,7 +51,22 @@ struct SceneDev {
   int32_t dtype;
   int32_t n_views;    // views rendering this scene (1 => gradients are stored, else added)
   int32_t pad_;
+  const float* filter_var;  // [n] Mip-Splatting 3D filter variances, or NULL
 };
+
+// Mip-Splatting 3D filter, the exactly rounded FP32 chain shared by the forward
+// (where it feeds the binning decisions) and the backward:
+// s~ = sqrt(s^2 + v), o' = ((o * (s0/s~0)) * (s1/s~1)) * (s2/s~2).
+__device__ inline void filter3d_apply(float v, float (&s)[3], float& o) {
+  float r[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float st = __fsqrt_rn(__fadd_rn(__fmul_rn(s[k], s[k]), v));
+    r[k] = __fdiv_rn(s[k], st);
+    s[k] = st;
+  }
+  o = __fmul_rn(__fmul_rn(__fmul_rn(o, r[0]), r[1]), r[2]);
+}
 
 struct FrameDev {
   ViewDev views[GS_MAX_VIEWS];
@@ -96,7 +111,8 @@ struct Header {
   unsigned long long n_evals_bwd;
   int32_t status;
   int32_t work_fwd, work_bwd;   // work-queue counters of the persistent compositing kernels
-  int32_t pad_[51];
+  uint32_t filter_max;          // bits of the largest 3D-filter variance of seen Gaussians
+  int32_t pad_[50];
 };
 
 // Byte offsets of every buffer inside the caller's workspace.
@@ -164,6 +180,8 @@ cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& host_fd
                               const gs_map_grads& g, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(void* ws, const Layout& L, const FrameDev& host_fd,
                                   const GradPtrs& gp, cudaStream_t s);
+cudaError_t launch_filter3d(void* ws, const Layout& L, const FrameDev& host_fd, int scene, float scale,
+                            float* out, cudaStream_t s);
 cudaError_t launch_nloss_fwd(void* ws, const Layout& L, const FrameDev& host_fd, float* nloss,
                              cudaStream_t s);
 cudaError_t launch_nloss_bwd(void* ws, const Layout& L, const FrameDev& host_fd, const float* dnloss,

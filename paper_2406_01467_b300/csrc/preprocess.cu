@@ -12,6 +12,8 @@
 // The chain that decides visibility, the pixel rectangle and the depth key is
 // evaluated with explicitly rounded FP32 operations in a fixed order, so that
 // the tile lists are reproducible bit for bit on any IEEE machine.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -279,6 +281,7 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
     const int64_t e = ch.e0 + t, g = ch.g0 + t;
     float m[3], s[3], q[4], o;
     load_gauss<T>(S, g, m, s, q, o);
+    if (S.filter_var) filter3d_apply(__ldg(S.filter_var + g), s, o);   // Mip-Splatting 3D filter
     float chk = 0.f;   // inf * 0 and nan * 0 are nan
     for (int k = 0; k < 3; ++k) chk += m[k] * 0.f + s[k] * 0.f;
     for (int k = 0; k < 4; ++k) chk += q[k] * 0.f;
@@ -475,6 +478,9 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
     } else {
       float m[3], s[3], q[4], o;
       load_gauss<T>(S, g, m, s, q, o);
+      const float s0[3] = {s[0], s[1], s[2]};
+      const float fv = S.filter_var ? __ldg(S.filter_var + g) : 0.f;
+      if (S.filter_var) filter3d_apply(fv, s, o);   // s, o: filtered scales and opacity
       float c[3 * K];
       load_sh<T, K>(S, g, c);
       Geo geo;
@@ -628,12 +634,83 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
       gx[1] += gv * V.fy * iz;
       gx[2] += -(gu * V.fx * gg.xc[0] + gv * V.fy * gg.xc[1]) * iz2 + gz_tot;
       for (int k = 0; k < 3; ++k) gm[k] += V.R[k] * gx[0] + V.R[3 + k] * gx[1] + V.R[6 + k] * gx[2];
+      // ---- 3D filter: s~ = sqrt(s^2 + v), o' = o prod s/s~ ------------------------------------------
+      if (S.filter_var) {
+        float rp = 1.f;
+        for (int k = 0; k < 3; ++k) rp *= s0[k] / s[k];
+        for (int k = 0; k < 3; ++k)
+          gsc[k] = gsc[k] * (s0[k] / s[k]) + go * o * fv / (s0[k] * s[k] * s[k]);
+        go *= rp;
+      }
     }
     if (Dg.dmeans) for (int k = 0; k < 3; ++k) put(Dg.dmeans, 3 * g + k, gm[k]);
     if (Dg.dscales) for (int k = 0; k < 3; ++k) put(Dg.dscales, 3 * g + k, gsc[k]);
     if (Dg.dquats) for (int k = 0; k < 4; ++k) put(Dg.dquats, 4 * g + k, gq[k]);
     if (Dg.dopacities) put(Dg.dopacities, g, go);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Mip-Splatting 3D filter variance from the cameras: v = c min_n (z_n / f_n)^2
+// over the views n of the scene in which the centre is in front of the near
+// plane and projects inside the image widened by 15 % on each side; Gaussians
+// seen by no view get the largest v of the seen ones.  Pass 1 writes v (or -1)
+// and folds the maximum into the header; pass 2 fills the unseen.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_filter3d(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, int scene,
+                           float scale, float* __restrict__ out) {
+  const SceneDev& S = fd->scenes[scene];
+  Header* hdr = at<Header>(ws, L.hdr);
+  const T* mp = static_cast<const T*>(S.means);
+  float vmax = 0.f;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < S.n; g += (int64_t)gridDim.x * blockDim.x) {
+    const float m0 = ldf<T>(mp, 3 * g), m1 = ldf<T>(mp, 3 * g + 1), m2 = ldf<T>(mp, 3 * g + 2);
+    float best = 3.4e38f;
+    bool seen = false;
+    for (int v = 0; v < fd->n_views; ++v) {
+      const ViewDev& V = fd->views[v];
+      if (V.scene != scene) continue;
+      const float x = V.R[0] * m0 + V.R[1] * m1 + V.R[2] * m2 + V.t[0];
+      const float y = V.R[3] * m0 + V.R[4] * m1 + V.R[5] * m2 + V.t[1];
+      const float z = V.R[6] * m0 + V.R[7] * m1 + V.R[8] * m2 + V.t[2];
+      if (!(z > V.near_plane)) continue;
+      const float u = V.fx * x / z + V.cx, w = V.fy * y / z + V.cy;
+      const float mw = 0.15f * V.width, mh = 0.15f * V.height;
+      if (u >= -mw && u <= V.width + mw && w >= -mh && w <= V.height + mh) {
+        const float r = z / V.fx;
+        best = fminf(best, r * r);
+        seen = true;
+      }
+    }
+    const float val = seen ? scale * best : -1.f;
+    out[g] = val;
+    vmax = fmaxf(vmax, val);
+  }
+  for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xFFFFFFFFu, vmax, o));
+  if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(&hdr->filter_max, __float_as_uint(vmax));
+}
+
+__global__ void k_filter3d_fill(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, int scene,
+                                float* __restrict__ out) {
+  const int64_t n = fd->scenes[scene].n;
+  const float fill = __uint_as_float(at<Header>(ws, L.hdr)->filter_max);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    if (out[g] < 0.f) out[g] = fill;
+}
+
+cudaError_t launch_filter3d(void* ws, const Layout& L, const FrameDev& hf, int scene, float scale, float* out,
+                            cudaStream_t s) {
+  const int64_t n = hf.scenes[scene].n;
+  if (n == 0) return cudaSuccess;
+  const FrameDev* fd = at<FrameDev>(ws, L.frame);
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
+  if (hf.scenes[scene].dtype == GS_BF16)
+    k_filter3d<__nv_bfloat16><<<grid, 256, 0, s>>>(fd, ws, L, scene, scale, out);
+  else
+    k_filter3d<float><<<grid, 256, 0, s>>>(fd, ws, L, scene, scale, out);
+  k_filter3d_fill<<<grid, 256, 0, s>>>(fd, ws, L, scene, out);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

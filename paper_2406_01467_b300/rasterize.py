@@ -57,6 +57,7 @@ class SceneTensors:
     opacities: torch.Tensor  # (N,)
     sh: torch.Tensor         # (N, (deg+1)^2, 3)
     sh_degree: int
+    filter_var: Optional[torch.Tensor] = None   # (N,) FP32 Mip-Splatting 3D filter variances
 
     @property
     def n(self) -> int:
@@ -69,8 +70,10 @@ class SceneTensors:
     @staticmethod
     def from_scene(scene, device="cuda", dtype=torch.float32) -> "SceneTensors":
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dtype).contiguous()
+        fv = getattr(scene, "filter_var", None)
+        fv = None if fv is None else torch.as_tensor(np.ascontiguousarray(fv, np.float32)).to(device)
         return SceneTensors(t(scene.means), t(scene.scales), t(scene.quats), t(scene.opacities),
-                            t(scene.sh), int(scene.sh_degree))
+                            t(scene.sh), int(scene.sh_degree), fv)
 
     def check(self):
         n = self.n
@@ -86,6 +89,10 @@ class SceneTensors:
                 raise ValueError(f"{k} has shape {tuple(a.shape)}, expected {shp}")
             if a.dtype != dt or not a.is_contiguous() or not a.is_cuda:
                 raise ValueError(f"{k} must be a contiguous CUDA tensor of dtype {dt}")
+        fv = self.filter_var
+        if fv is not None and (tuple(fv.shape) != (n,) or fv.dtype != torch.float32 or not fv.is_contiguous()
+                               or not fv.is_cuda):
+            raise ValueError("filter_var must be a contiguous CUDA float32 tensor of shape (N,)")
 
 
 def view_struct(cam, scene_index: int = 0) -> GsView:
@@ -147,7 +154,7 @@ class Frame:
     def _bind_scenes(self):
         for i, s in enumerate(self.scenes):
             self._c_scenes[i] = GsScene(_ptr(s.means), _ptr(s.scales), _ptr(s.quats), _ptr(s.opacities),
-                                        _ptr(s.sh), s.n, s.sh_degree, s.dtype_code)
+                                        _ptr(s.sh), s.n, s.sh_degree, s.dtype_code, _ptr(s.filter_var))
 
     def rebind(self, scenes: Sequence[SceneTensors]):
         """Point the frame at new parameter tensors of the same shapes."""
@@ -201,6 +208,18 @@ class Frame:
             if self.last_status not in (GS_OK, _lib.GS_ERR_NUMERIC):
                 check(self.last_status, "binning")
         self.render(stream)
+
+    def filter3d(self, scene: int = 0, scale: float = 0.2, attach: bool = True, stream=None):
+        """Mip-Splatting 3D filter variances of ``scene`` from this frame's views of it
+        (FP32 (N,)); with ``attach`` the scene renders with them from now on."""
+        s = self.scenes[scene]
+        out = torch.empty(s.n, dtype=torch.float32, device=self.device)
+        check(self.lib.gs_filter3d(ctypes.byref(self.frame), int(scene), float(scale), _ptr(out),
+                                   _stream(stream)), "gs_filter3d")
+        if attach:
+            s.filter_var = out
+            self._bind_scenes()
+        return out
 
     def alloc_grads(self):
         out = []
