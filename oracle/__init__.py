@@ -17,11 +17,17 @@ Layout
 ``composite``  per-pixel front-to-back alpha blending (Eq. 3) of colour, alpha,
                planar depth (Eq. 4) and normal, with the median depth (Sec. 1);
                gradients by torch autograd in FP64.
+``losses``     depth distortion (Eq. 23, weights detached) and normal consistency
+               (Eq. 24, normals of the depth map by central differences).
+``filter3d``   the Mip-Splatting 3D filter (Sigma + v I with opacity compensation)
+               and its per-Gaussian variance from the cameras (Sec. 4.1.1).
+``appearance`` decoupled per-view appearance (Sec. 4.1.1): embedding -> MLP ->
+               colour affine, L1 loss, Adam.
 
 Parity pins: every function is checked against a value the paper or
 mathematics fixes (closed forms, library routines, invariants, brute force,
 finite differences) by the ``-m "not gpu"`` tests.
 """
 from .params import RenderParams  # noqa: F401
-from . import sh, gaussians, binning, composite, losses, filter3d  # noqa: F401
+from . import sh, gaussians, binning, composite, losses, filter3d, appearance  # noqa: F401
 from .render import render, render_grads  # noqa: F401
