@@ -235,6 +235,51 @@ gs_status gs_preprocess_bwd(const gs_frame* frame, const gs_scene_grads* grads, 
  * workspace's counters and status like gs_preprocess. */
 gs_status gs_filter3d(const gs_frame* frame, int32_t scene, float scale, float* filter_var, void* stream);
 
+/* ---- Decoupled per-view appearance (Sec. 4.1.1, after VastGaussian) -------
+ * The paper trains with a learned per-view colour correction so that exposure
+ * and white-balance changes between photographs are not baked into the
+ * Gaussians.  Here each training view owns an embedding e (embed_dim floats);
+ * a two-layer perceptron h = relu(W1 e + b1), a = W2 h + b2 (12 outputs) gives
+ * the affine c' = (I + A) c + t of the rendered colour, A = a[0..8] row-major,
+ * t = a[9..11].  The loss of a view is the mean over its pixels and channels of
+ * |c' - target|.  With W2 = b2 = 0 the correction is the identity.
+ *
+ * params / grads: device FP32 [gs_appearance_param_count()], flat layout
+ *   embed [n_embeddings][embed_dim], W1 [hidden][embed_dim], b1 [hidden],
+ *   W2 [12][hidden], b2 [12]. */
+typedef struct {
+  int32_t n_embeddings; /* >= 1: one per training view */
+  int32_t embed_dim;    /* 1..256 */
+  int32_t hidden;       /* 1..256 */
+  int32_t pad_;
+  float* params;
+  float* grads;         /* gs_appearance_fwd_bwd adds to it */
+} gs_appearance;
+
+/* Floats of device scratch gs_appearance_fwd_bwd needs per view. */
+#define GS_APPEARANCE_STATE_FLOATS 32
+
+/* Parameters of an appearance model; 0 (and the error string) on bad sizes. */
+size_t gs_appearance_param_count(int32_t n_embeddings, int32_t embed_dim, int32_t hidden);
+
+/* For every view of `frame` (only its views' sizes are used): the affine from
+ * embedding row embed_index[v] (host array [n_views]), the corrected colour
+ * (written to `corrected` if not NULL), the loss (device [n_views], if not
+ * NULL), dL/dc into `dcolor` (if not NULL; overwritten, the colour gradient
+ * for gs_render_bwd), and dL/d(params) added to app->grads.  color, target,
+ * corrected and dcolor are device FP32 maps in the gs_maps colour layout;
+ * state is device scratch of GS_APPEARANCE_STATE_FLOATS * n_views floats. */
+gs_status gs_appearance_fwd_bwd(const gs_frame* frame, const gs_appearance* app, const int32_t* embed_index,
+                                const float* color, const float* target, float* corrected, float* dcolor,
+                                float* loss, float* state, void* stream);
+
+/* One Adam step (Kingma and Ba) on n FP32 parameters, `step` >= 1 counting
+ * from 1: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps); then g = 0 if
+ * zero_grads.  All buffers device FP32 [n]. */
+gs_status gs_adam_step(float* params, float* grads, float* m, float* v, int64_t n, float lr, float beta1,
+                       float beta2, float eps, int32_t step, int32_t zero_grads, void* stream);
+
 /* Intermediate results for tests and tools, copied to caller device buffers on
  * `stream`; any pointer may be NULL.  rec: [n_entries][16] FP32 per-entry
  * records (u, v, conic a b c, opacity, sigma cut, z, p0 p1, n0 n1 n2, r g b);

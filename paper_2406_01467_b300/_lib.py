@@ -61,6 +61,14 @@ class GsSceneGrads(Structure):
                 ("dopacities", c_void_p), ("dsh", c_void_p)]
 
 
+class GsAppearance(Structure):
+    _fields_ = [("n_embeddings", c_int32), ("embed_dim", c_int32), ("hidden", c_int32), ("pad_", c_int32),
+                ("params", c_void_p), ("grads", c_void_p)]
+
+
+APPEARANCE_STATE_FLOATS = 32
+
+
 class GsStats(Structure):
     _fields_ = [("n_entries", c_int64), ("n_visible", c_int64), ("n_pairs", c_int64),
                 ("n_nonfinite", c_int64), ("n_evals_fwd", c_int64), ("n_evals_bwd", c_int64),
@@ -68,7 +76,8 @@ class GsStats(Structure):
 
 
 EXPORTS = ("gs_workspace_size", "gs_preprocess", "gs_bin", "gs_render_fwd", "gs_render_bwd",
-           "gs_composite_bwd", "gs_preprocess_bwd", "gs_filter3d", "gs_debug_copy", "gs_render_fwd_static",
+           "gs_composite_bwd", "gs_preprocess_bwd", "gs_filter3d", "gs_appearance_param_count",
+           "gs_appearance_fwd_bwd", "gs_adam_step", "gs_debug_copy", "gs_render_fwd_static",
            "gs_check", "gs_last_error_string")
 STATIC_SCRATCH_BYTES = 32 << 20
 
@@ -106,6 +115,14 @@ def load(path: str = LIB_PATH):
     lib.gs_preprocess_bwd.restype = c_int32
     lib.gs_filter3d.argtypes = [pf, c_int32, c_float, c_void_p, c_void_p]
     lib.gs_filter3d.restype = c_int32
+    lib.gs_appearance_param_count.argtypes = [c_int32, c_int32, c_int32]
+    lib.gs_appearance_param_count.restype = c_size_t
+    lib.gs_appearance_fwd_bwd.argtypes = [pf, POINTER(GsAppearance), c_void_p, c_void_p, c_void_p, c_void_p,
+                                          c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.gs_appearance_fwd_bwd.restype = c_int32
+    lib.gs_adam_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_float, c_float,
+                                 c_float, c_int32, c_int32, c_void_p]
+    lib.gs_adam_step.restype = c_int32
     lib.gs_debug_copy.argtypes = [pf, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p]
     lib.gs_debug_copy.restype = c_int32

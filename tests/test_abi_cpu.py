@@ -141,3 +141,15 @@ def test_geometry_only_drops_the_backward_state(lib):
     assert "no backward" in lib.gs_last_error_string().decode()
     f.params.losses = 1
     assert lib.gs_workspace_size(ctypes.byref(f)) == 0
+
+
+def test_appearance_param_count_and_validation(lib):
+    assert lib.gs_appearance_param_count(10, 32, 64) == 10 * 32 + 64 * 32 + 64 + 12 * 64 + 12
+    assert lib.gs_appearance_param_count(10, 300, 64) == 0
+    assert "embed_dim" in lib.gs_last_error_string().decode()
+    f = _frame()
+    app = _lib.GsAppearance(2, 8, 8, 0, 256, 256)
+    idx = (ctypes.c_int32 * 1)(5)   # out of range: refused before any device work
+    st = lib.gs_appearance_fwd_bwd(ctypes.byref(f), ctypes.byref(app), idx, 256, 256, None, None, None, 256, None)
+    assert st == _lib.GS_ERR_INVALID_ARG and "embedding index" in lib.gs_last_error_string().decode()
+    assert lib.gs_adam_step(256, 256, 256, 256, 10, 0.01, 0.9, 0.999, 1e-8, 0, 1, None) == _lib.GS_ERR_INVALID_ARG
