@@ -126,14 +126,36 @@ __device__ inline bool reaches(const float4& f0, const float4& f1, const SubRect
   return rect_min_sigma(f0.x, f0.y, f0.z, f0.w, f1.x, ia, ic, R.X0, R.X1, R.Y0, R.Y1) <= f1.z;
 }
 
+// Asynchronous global->shared copies (cp.async): each lane stages whole
+// 64-byte records, so the next chunk's gathers are in flight while the warp
+// evaluates the current one.
+__device__ inline void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ inline void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// A chunk buffer is slot-major ([4][32] float4): lane l's 16-byte pieces sit
+// 512 bytes apart, so per-lane accesses are free of bank conflicts.
+__device__ inline void stage_record(float4 (*chunk)[32], int lane, const float4* r) {
+  const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(&chunk[0][lane]));
+  cp_async16(dst, r);
+  cp_async16(dst + 512, r + 1);
+  cp_async16(dst + 1024, r + 2);
+  cp_async16(dst + 1536, r + 3);
+}
+
 // One work item: warp-sized block `sub` of tile `tile`.  The warp walks the
-// tile's list on its own, 32 records at a time: every lane loads one record's
-// first half and tests it against the warp's rectangle; the records that pass
-// are staged whole in the warp's shared slots and evaluated by all 32 lanes in
-// list order.  The walk ends as soon as the block's own pixels are done.
+// tile's list on its own, 32 records at a time, through two shared buffers:
+// while it evaluates chunk k (every lane tests one record against the warp's
+// rectangle, then the records that pass are evaluated by all 32 lanes in list
+// order), the records of chunk k+1 are being copied in, and the entry indices
+// of chunk k+2 are being loaded.  The walk ends as soon as the block's own
+// pixels are done (after the copies in flight have landed).
 template <bool LOSS, bool GEO>
 __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restrict__ ws, const Layout& L,
-                                const gs_maps& maps, int tile, int sub, float4 (*my)[4], uint32_t& evals) {
+                                const gs_maps& maps, int tile, int sub, float4 (*buf)[4][32], uint32_t& evals) {
   const TileCtx c = tile_ctx(fd, tile, sub);
   const int2 range = at<int2>(ws, L.ranges)[tile];
   const uint32_t* pval = at<uint32_t>(ws, L.pval_final);
@@ -147,29 +169,29 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   float Ws = 0.f, S1 = 0.f, S2 = 0.f, d0 = 0.f;   // Eq. 23 moments (LOSS only)
   int last = -1, med = -1;
   bool done = !c.inside;
+  int cur = 0;
+  uint32_t e_next = 0;   // entry of this lane's record in the chunk after the one in flight
+  if (range.x < range.y) {
+    if (range.x + lane < range.y) stage_record(buf[0], lane, rec + 4 * (int64_t)__ldg(pval + range.x + lane));
+    cp_async_commit();
+    if (range.x + 32 + lane < range.y) e_next = __ldg(pval + range.x + 32 + lane);
+  }
   for (int c0 = range.x; c0 < range.y; c0 += 32) {
     if (__all_sync(kFull, done)) break;
-    const int i = c0 + lane;
-    bool rel = false;
-    if (i < range.y) {
-      const float4* r = rec + 4 * (int64_t)pval[i];
-      const float4 f0 = __ldg(r), f1 = __ldg(r + 1);
-      rel = reaches(f0, f1, R);
-      if (rel) {
-        my[lane][0] = f0;
-        my[lane][1] = f1;
-        my[lane][2] = __ldg(r + 2);
-        my[lane][3] = __ldg(r + 3);
-      }
-    }
+    if (c0 + 32 + lane < range.y) stage_record(buf[cur ^ 1], lane, rec + 4 * (int64_t)e_next);
+    cp_async_commit();
+    if (c0 + 64 + lane < range.y) e_next = __ldg(pval + c0 + 64 + lane);
+    cp_async_wait<1>();     // this lane's copies of chunk c0 have landed
+    __syncwarp();           // ... and every lane's are visible
+    float4 (*my)[32] = buf[cur];
+    const bool rel = c0 + lane < range.y && reaches(my[0][lane], my[1][lane], R);
     unsigned m = __ballot_sync(kFull, rel);
-    __syncwarp();
     while (m) {
       const int j = __ffs(m) - 1;
       m &= m - 1;
       if (done) continue;
       ++evals;
-      const float4 a = my[j][0], b = my[j][1];
+      const float4 a = my[0][j], b = my[1][j];
       const float dx = a.x - fpx, dy = a.y - fpy;
       const float sig = quad(a.z, a.w, b.x, dx, dy);
       const float al = fminf(amax, b.y * __expf(-sig));
@@ -177,7 +199,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float Tn = T * (1.f - al);
       if (Tn < tmin) { done = true; continue; }
       const float w = al * T;
-      const float4 e2 = my[j][2], e3 = my[j][3];
+      const float4 e2 = my[2][j], e3 = my[3][j];
       if (!GEO) { C0 += w * e3.y; C1 += w * e3.z; C2 += w * e3.w; }
       N0 += w * e2.z; N1 += w * e2.w; N2 += w * e3.x;
       const float dk = b.w + e2.x * dx + e2.y * dy;   // Eq. 4
@@ -195,8 +217,11 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       last = c0 + j;
       T = Tn;
     }
-    __syncwarp();
+    __syncwarp();           // buf[cur] is refilled two chunks later
+    cur ^= 1;
   }
+  cp_async_wait<0>();       // no copy may land in the buffers after the item
+  __syncwarp();
   if (!c.inside) return;
   if (med < 0 && last >= 0) {   // median never reached: depth of the last contributor
     med = last;
@@ -270,7 +295,7 @@ __device__ inline float warp_reduce_scatter16(float (&v)[16]) {
 // its pixels from their last contributors toward the front of the list.
 template <bool LOSS>
 __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restrict__ ws, const Layout& L,
-                                const gs_map_grads& g, int tile, int sub, float4 (*my)[4], uint32_t* my_e,
+                                const gs_map_grads& g, int tile, int sub, float4 (*my)[32], uint32_t* my_e,
                                 uint32_t& evals) {
   const TileCtx c = tile_ctx(fd, tile, sub);
   const int2 range = at<int2>(ws, L.ranges)[tile];
@@ -330,10 +355,10 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float4 f0 = __ldg(r), f1 = __ldg(r + 1);
       rel = reaches(f0, f1, R);
       if (rel) {
-        my[lane][0] = f0;
-        my[lane][1] = f1;
-        my[lane][2] = __ldg(r + 2);
-        my[lane][3] = __ldg(r + 3);
+        my[0][lane] = f0;
+        my[1][lane] = f1;
+        my[2][lane] = __ldg(r + 2);
+        my[3][lane] = __ldg(r + 3);
         my_e[lane] = e;
       }
     }
@@ -349,7 +374,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       bool contrib = false;
       if (idx <= last) {
         ++evals;
-        const float4 a = my[j][0], b = my[j][1];
+        const float4 a = my[0][j], b = my[1][j];
         const float dx = a.x - fpx, dy = a.y - fpy;
         const float sig = quad(a.z, a.w, b.x, dx, dy);
         const float G = __expf(-sig);
@@ -357,7 +382,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
         const float al = fminf(amax, raw);
         if (al >= amin) {
           contrib = true;
-          const float4 e2 = my[j][2], e3 = my[j][3];
+          const float4 e2 = my[2][j], e3 = my[3][j];
           const float rgb[3] = {e3.y, e3.z, e3.w}, nrm[3] = {e2.z, e2.w, e3.x};
           const float ia = __fdividef(1.f, 1.f - al);
           T *= ia;                         // transmittance in front of this splat
@@ -424,10 +449,10 @@ template <bool LOSS, bool GEO>
 __global__ void __launch_bounds__(kRenderThreads)
 k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_maps maps, int subs,
              int n_items) {
-  __shared__ float4 s_rec[kRenderThreads / 32][32][4];
+  __shared__ float4 s_rec[kRenderThreads / 32][2][4][32];
   Header* hdr = at<Header>(ws, L.hdr);
   if (hdr->status == GS_ERR_CAPACITY) return;
-  float4 (*my)[4] = s_rec[threadIdx.x >> 5];
+  float4 (*buf)[4][32] = s_rec[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   uint32_t evals = 0;
   for (;;) {
@@ -435,7 +460,7 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     if (lane == 0) item = atomicAdd(&hdr->work_fwd, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= n_items) break;
-    fwd_item<LOSS, GEO>(fd, ws, L, maps, item / subs, item % subs, my, evals);
+    fwd_item<LOSS, GEO>(fd, ws, L, maps, item / subs, item % subs, buf, evals);
     __syncwarp();
   }
   count_evals(evals, &hdr->n_evals_fwd);
@@ -445,11 +470,11 @@ template <bool LOSS>
 __global__ void __launch_bounds__(kRenderThreads)
 k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_map_grads g, int subs,
              int n_items) {
-  __shared__ float4 s_rec[kRenderThreads / 32][32][4];
+  __shared__ float4 s_rec[kRenderThreads / 32][4][32];
   __shared__ uint32_t s_ent[kRenderThreads / 32][32];
   Header* hdr = at<Header>(ws, L.hdr);
   if (hdr->status == GS_ERR_CAPACITY) return;
-  float4 (*my)[4] = s_rec[threadIdx.x >> 5];
+  float4 (*my)[32] = s_rec[threadIdx.x >> 5];
   uint32_t* my_e = s_ent[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   uint32_t evals = 0;
