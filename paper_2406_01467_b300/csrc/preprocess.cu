@@ -443,7 +443,8 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
 // ---------------------------------------------------------------------------
 // Backward: d(record) -> d(means, scales, quats, opacities, sh)
 // ---------------------------------------------------------------------------
-template <typename T, int D>
+// FILT: the scene carries Mip-Splatting 3D filter variances.
+template <typename T, int D, bool FILT>
 __global__ void __launch_bounds__(kPreThreads)
 k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, GradPtrs gp) {
   constexpr int K = (D + 1) * (D + 1);
@@ -454,7 +455,7 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
     const Chunk ch = chunk_of(fd, bi);
     const ViewDev& V = fd->views[ch.view];
     const SceneDev& S = fd->scenes[V.scene];
-    if (S.dtype != dtype_code<T>() || S.sh_degree != D) continue;
+    if (S.dtype != dtype_code<T>() || S.sh_degree != D || (S.filter_var != nullptr) != FILT) continue;
     const int t = threadIdx.x;
     if (t >= ch.n) continue;
     const gs_scene_grads& Dg = gp.g[V.scene];
@@ -479,8 +480,8 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
       float m[3], s[3], q[4], o;
       load_gauss<T>(S, g, m, s, q, o);
       const float s0[3] = {s[0], s[1], s[2]};
-      const float fv = S.filter_var ? __ldg(S.filter_var + g) : 0.f;
-      if (S.filter_var) filter3d_apply(fv, s, o);   // s, o: filtered scales and opacity
+      const float fv = FILT ? __ldg(S.filter_var + g) : 0.f;
+      if (FILT) filter3d_apply(fv, s, o);   // s, o: filtered scales and opacity
       float c[3 * K];
       load_sh<T, K>(S, g, c);
       Geo geo;
@@ -635,7 +636,7 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
       gx[2] += -(gu * V.fx * gg.xc[0] + gv * V.fy * gg.xc[1]) * iz2 + gz_tot;
       for (int k = 0; k < 3; ++k) gm[k] += V.R[k] * gx[0] + V.R[3 + k] * gx[1] + V.R[6 + k] * gx[2];
       // ---- 3D filter: s~ = sqrt(s^2 + v), o' = o prod s/s~ ------------------------------------------
-      if (S.filter_var) {
+      if (FILT) {
         float rp = 1.f;
         for (int k = 0; k < 3; ++k) rp *= s0[k] / s[k];
         for (int k = 0; k < 3; ++k)
@@ -732,31 +733,33 @@ static cudaError_t fwd_t(int deg, const FrameDev* fd, void* ws, const Layout& L,
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool FILT>
 static cudaError_t bwd_t(int deg, const FrameDev* fd, void* ws, const Layout& L, const GradPtrs& gp, int grid,
                          cudaStream_t s) {
   switch (deg) {
-    case 0: k_preprocess_bwd<T, 0><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
-    case 1: k_preprocess_bwd<T, 1><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
-    case 2: k_preprocess_bwd<T, 2><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
-    default: k_preprocess_bwd<T, 3><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
+    case 0: k_preprocess_bwd<T, 0, FILT><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
+    case 1: k_preprocess_bwd<T, 1, FILT><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
+    case 2: k_preprocess_bwd<T, 2, FILT><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
+    default: k_preprocess_bwd<T, 3, FILT><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
   }
   return cudaGetLastError();
 }
 
-// Bit (4 * dtype + degree) set for every kind of scene that a view renders.
+// Bit (4 * dtype + degree), plus 8 when the scene is filtered, set for every
+// kind of scene that a view renders.
 static unsigned kinds(const FrameDev& hf) {
   unsigned k = 0;
   for (int v = 0; v < hf.n_views; ++v) {
     const SceneDev& S = hf.scenes[hf.views[v].scene];
-    if (S.n > 0) k |= 1u << (4 * S.dtype + S.sh_degree);
+    if (S.n > 0) k |= 1u << (4 * S.dtype + S.sh_degree + (S.filter_var ? 8 : 0));
   }
   return k;
 }
 
 cudaError_t launch_preprocess(void* ws, const Layout& L, const FrameDev& hf, cudaStream_t s) {
   const FrameDev* fd = at<FrameDev>(ws, L.frame);
-  const unsigned k = kinds(hf);
+  const unsigned k0 = kinds(hf);
+  const unsigned k = (k0 | (k0 >> 8)) & 0xFFu;   // the forward reads the filter at run time
   const int grid = grid_chunks(hf.n_chunks);
   cudaError_t e = cudaSuccess;
   if (hf.geometry_only) {   // one launch per dtype, SH not read
@@ -778,8 +781,12 @@ cudaError_t launch_preprocess_bwd(void* ws, const Layout& L, const FrameDev& hf,
   const int grid = grid_chunks(hf.n_chunks);
   cudaError_t e = cudaSuccess;
   for (int deg = 0; deg < 4 && e == cudaSuccess; ++deg) {
-    if (k & (1u << (4 * GS_F32 + deg))) e = bwd_t<float>(deg, fd, ws, L, gp, grid, s);
-    if (e == cudaSuccess && (k & (1u << (4 * GS_BF16 + deg)))) e = bwd_t<__nv_bfloat16>(deg, fd, ws, L, gp, grid, s);
+    if (k & (1u << (4 * GS_F32 + deg))) e = bwd_t<float, false>(deg, fd, ws, L, gp, grid, s);
+    if (e == cudaSuccess && (k & (1u << (4 * GS_BF16 + deg))))
+      e = bwd_t<__nv_bfloat16, false>(deg, fd, ws, L, gp, grid, s);
+    if (e == cudaSuccess && (k & (1u << (8 + 4 * GS_F32 + deg)))) e = bwd_t<float, true>(deg, fd, ws, L, gp, grid, s);
+    if (e == cudaSuccess && (k & (1u << (8 + 4 * GS_BF16 + deg))))
+      e = bwd_t<__nv_bfloat16, true>(deg, fd, ws, L, gp, grid, s);
   }
   return e;
 }
