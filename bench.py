@@ -157,7 +157,7 @@ def launches_per_step(n_tiles, n_dtypes=1):
     bits = max(1, int(np.ceil(np.log2(max(n_tiles, 2)))))
     tile_passes = (bits + 7) // 8
     setup, pre = 1, n_dtypes
-    binning = 3 + 4 * 3 + 2 + 2 + 3 * tile_passes + 1
+    binning = 3 + 4 * 3 + 2 + 2 + 3 * tile_passes + 1 + 1   # ... ranges, work order
     return setup + pre + binning + 1 + 1 + n_dtypes
 
 

@@ -175,6 +175,7 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   L.hist = take(4 * (size_t)kRadix * nbmax);
   L.htot = take(4 * (size_t)kRadix);
   L.ranges = take(8 * (size_t)T);
+  L.tile_order = take(4 * (size_t)T);
   const bool bwd_state = !p.geometry_only;   // per-pixel replay state and 2D gradients
   L.px_T = take(bwd_state ? 4 * (size_t)NPIX : 0);
   L.px_last = take(bwd_state ? 4 * (size_t)NPIX : 0);

@@ -419,6 +419,33 @@ k_ranges(const uint32_t* __restrict__ ptile, const unsigned long long* n_pairs_p
   }
 }
 
+// Work order of the compositing kernels: tiles by decreasing list length
+// (buckets of equal floor(log2(length)), heaviest bucket first), so that the
+// longest items start first and the persistent kernels end on short ones.  One
+// block; the order inside a bucket is arbitrary (each pixel is computed by one
+// warp whatever the order).
+__global__ void __launch_bounds__(1024) k_tile_order(const int2* __restrict__ ranges, int T, int* __restrict__ order) {
+  __shared__ int cnt[32], off[32];
+  if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < T; t += blockDim.x) {
+    const int2 r = ranges[t];
+    const int len = r.y - r.x;
+    atomicAdd(&cnt[len > 0 ? 31 - __clz(len) : 0], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 31; b >= 0; --b) { off[b] = acc; acc += cnt[b]; }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < T; t += blockDim.x) {
+    const int2 r = ranges[t];
+    const int len = r.y - r.x;
+    order[atomicAdd(&off[len > 0 ? 31 - __clz(len) : 0], 1)] = t;
+  }
+}
+
 // ---------------------------------------------------------------------------
 static cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                               const unsigned long long* count, int64_t cap, int nb, int bits,
@@ -479,6 +506,8 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   cudaMemsetAsync(at<int2>(ws, L.ranges), 0, sizeof(int2) * (size_t)L.T, s);
   int g = (int)std::min<int64_t>((L.Pcap + 255) / 256, 148 * 32);
   k_ranges<<<g, 256, 0, s>>>(ptile, &hdr->n_pairs, L.Pcap, at<int2>(ws, L.ranges));
+  // 7. compositing work order
+  if (L.T > 0) k_tile_order<<<1, 1024, 0, s>>>(at<int2>(ws, L.ranges), (int)L.T, at<int>(ws, L.tile_order));
   return cudaGetLastError();
 }
 

@@ -257,38 +257,43 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   }
 }
 
-// Transposed warp reduce-scatter of 16 values: afterwards lane l holds the
-// warp-wide sum of slot (l >> 1) (lanes l and l^1 hold the same value).
-__device__ inline float warp_reduce_scatter16(float (&v)[16]) {
+// Transposed warp reduce-scatter of 16 values held as 8 pairs (v[k] = slots
+// 2k, 2k+1): afterwards lane l holds the warp-wide sum of slot (l >> 1)
+// (lanes l and l^1 hold the same value).  The additions are packed FP32x2.
+__device__ inline float warp_reduce_scatter16(float2 (&v)[8]) {
   const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  {
     const bool hi = lane & 16;
-    const float send = hi ? v[i] : v[i + 8];
-    const float keep = hi ? v[i + 8] : v[i];
-    v[i] = keep + __shfl_xor_sync(kFull, send, 16);
-  }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const bool hi = lane & 8;
-    const float send = hi ? v[i] : v[i + 4];
-    const float keep = hi ? v[i + 4] : v[i];
-    v[i] = keep + __shfl_xor_sync(kFull, send, 8);
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const bool hi = lane & 4;
-    const float send = hi ? v[i] : v[i + 2];
-    const float keep = hi ? v[i + 2] : v[i];
-    v[i] = keep + __shfl_xor_sync(kFull, send, 4);
+    for (int k = 0; k < 4; ++k) {   // slots 2k, 2k+1 vs 2k+8, 2k+9
+      const float2 send = hi ? v[k] : v[k + 4];
+      const float2 keep = hi ? v[k + 4] : v[k];
+      const float2 recv = make_float2(__shfl_xor_sync(kFull, send.x, 16), __shfl_xor_sync(kFull, send.y, 16));
+      v[k] = __fadd2_rn(keep, recv);
+    }
   }
   {
-    const bool hi = lane & 2;
-    const float send = hi ? v[0] : v[1];
-    const float keep = hi ? v[1] : v[0];
-    v[0] = keep + __shfl_xor_sync(kFull, send, 2);
+    const bool hi = lane & 8;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float2 send = hi ? v[k] : v[k + 2];
+      const float2 keep = hi ? v[k + 2] : v[k];
+      const float2 recv = make_float2(__shfl_xor_sync(kFull, send.x, 8), __shfl_xor_sync(kFull, send.y, 8));
+      v[k] = __fadd2_rn(keep, recv);
+    }
   }
-  return v[0] + __shfl_xor_sync(kFull, v[0], 1);
+  {
+    const bool hi = lane & 4;
+    const float2 send = hi ? v[0] : v[1];
+    const float2 keep = hi ? v[1] : v[0];
+    const float2 recv = make_float2(__shfl_xor_sync(kFull, send.x, 4), __shfl_xor_sync(kFull, send.y, 4));
+    v[0] = __fadd2_rn(keep, recv);
+  }
+  const bool hi = lane & 2;
+  const float send = hi ? v[0].x : v[0].y;
+  const float keep = hi ? v[0].y : v[0].x;
+  const float r = keep + __shfl_xor_sync(kFull, send, 2);
+  return r + __shfl_xor_sync(kFull, r, 1);
 }
 
 // One backward work item (same decomposition as fwd_item): the warp replays
@@ -345,7 +350,11 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
 
   float T = Tf;
   const float dATf = dA * Tf;
-  float Sc[3] = {0.f, 0.f, 0.f}, Sn[3] = {0.f, 0.f, 0.f};
+  // running "behind" sums of (r, g, b, n0, n1, n2) and the upstream of the same six, as pairs
+  float2 S01 = make_float2(0.f, 0.f), S23 = make_float2(0.f, 0.f), S45 = make_float2(0.f, 0.f);
+  const float2 U01 = make_float2(dC[0], dC[1]), U23 = make_float2(dC[2], dN[0]), U45 = make_float2(dN[1], dN[2]);
+  const float2 dN01 = make_float2(dN[0], dN[1]), dN2C0 = make_float2(dN[2], dC[0]), dC12 = make_float2(dC[1], dC[2]);
+  const float2 nfp = make_float2(-fpx, -fpy);
   for (int c1 = wmax + 1; c1 > range.x; c1 -= 32) {
     const int i = c1 - 1 - lane;          // lane 0 holds the farthest record of the chunk
     bool rel = false;
@@ -368,64 +377,72 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const int j = __ffs(m) - 1;
       m &= m - 1;
       const int idx = c1 - 1 - j;
-      float gr[16];
+      // gradient slots as pairs: (U,V) (CA,CB) (CC,O) (CUT,Z) (P0,P1) (N0,N1) (N2,R) (G,B)
+      float2 gr[8];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) gr[k] = 0.f;
+      for (int k = 0; k < 8; ++k) gr[k] = make_float2(0.f, 0.f);
       bool contrib = false;
       if (idx <= last) {
         ++evals;
         const float4 a = my[0][j], b = my[1][j];
-        const float dx = a.x - fpx, dy = a.y - fpy;
-        const float sig = quad(a.z, a.w, b.x, dx, dy);
+        const float2 d = __fadd2_rn(make_float2(a.x, a.y), nfp);     // (dx, dy)
+        const float dx = d.x, dy = d.y;
+        const float2 d2 = __fmul2_rn(d, d);                           // (dx^2, dy^2)
+        const float sig = 0.5f * (a.z * d2.x + b.x * d2.y) + a.w * dx * dy;
         const float G = __expf(-sig);
         const float raw = b.y * G;
         const float al = fminf(amax, raw);
         if (al >= amin) {
           contrib = true;
           const float4 e2 = my[2][j], e3 = my[3][j];
-          const float rgb[3] = {e3.y, e3.z, e3.w}, nrm[3] = {e2.z, e2.w, e3.x};
           const float ia = __fdividef(1.f, 1.f - al);
           T *= ia;                         // transmittance in front of this splat
           const float w = al * T;
-          gr[R_R] = w * dC[0]; gr[R_G] = w * dC[1]; gr[R_B] = w * dC[2];
-          gr[R_N0] = w * dN[0]; gr[R_N1] = w * dN[1]; gr[R_N2] = w * dN[2];
+          const float2 w2 = make_float2(w, w);
+          // colour and normal: (rgb, n) and the upstream (dC, dN) as three pairs
+          const float2 x0 = make_float2(e3.y, e3.z), x1 = make_float2(e3.w, e2.z), x2 = make_float2(e2.w, e3.x);
+          gr[5] = __fmul2_rn(w2, dN01);
+          gr[6] = __fmul2_rn(w2, dN2C0);
+          gr[7] = __fmul2_rn(w2, dC12);
           // (x - S) enters both dL/dalpha and the update S += alpha (x - S)
-          float dsum = 0.f;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const float dc = rgb[k] - Sc[k], dn = nrm[k] - Sn[k];
-            dsum += dc * dC[k] + dn * dN[k];
-            Sc[k] += al * dc;
-            Sn[k] += al * dn;
-          }
-          const float dal = T * dsum + dATf * ia;
+          const float2 q0 = __fadd2_rn(x0, make_float2(-S01.x, -S01.y));
+          const float2 q1 = __fadd2_rn(x1, make_float2(-S23.x, -S23.y));
+          const float2 q2 = __fadd2_rn(x2, make_float2(-S45.x, -S45.y));
+          float2 acc = __fmul2_rn(q0, U01);
+          acc = __ffma2_rn(q1, U23, acc);
+          acc = __ffma2_rn(q2, U45, acc);
+          const float2 al2 = make_float2(al, al);
+          S01 = __ffma2_rn(al2, q0, S01);
+          S23 = __ffma2_rn(al2, q1, S23);
+          S45 = __ffma2_rn(al2, q2, S45);
+          const float dal = T * (acc.x + acc.y) + dATf * ia;
           float gu = 0.f, gv = 0.f;
           if (LOSS) {                  // d = z_c + p . Delta (Eq. 4), median and Eq. 23
             const float dk = b.w + e2.x * dx + e2.y * dy;
             const float sd = c4 * w * (dk - dmean) + (idx == med ? dD : 0.f);
-            gr[R_Z] = sd;
-            gr[R_P0] = sd * dx;
-            gr[R_P1] = sd * dy;
+            gr[3].y = sd;
+            gr[4] = __fmul2_rn(make_float2(sd, sd), d);
             gu += sd * e2.x;
             gv += sd * e2.y;
           } else if (idx == med) {     // d = z_c + p . Delta (Eq. 4)
-            gr[R_Z] = dD;
-            gr[R_P0] = dD * dx;
-            gr[R_P1] = dD * dy;
+            gr[3].y = dD;
+            gr[4] = __fmul2_rn(make_float2(dD, dD), d);
             gu += dD * e2.x;
             gv += dD * e2.y;
           }
           if (raw <= amax) {
-            gr[R_O] = dal * G;
             const float gs = -dal * al;
-            gr[R_CA] = 0.5f * gs * dx * dx;
-            gr[R_CB] = gs * dx * dy;
-            gr[R_CC] = 0.5f * gs * dy * dy;
-            gu += gs * (a.z * dx + a.w * dy);
-            gv += gs * (a.w * dx + b.x * dy);
+            const float2 hgs = make_float2(0.5f * gs, 0.5f * gs);
+            const float2 cac = __fmul2_rn(hgs, d2);        // (CA, CC)
+            gr[1] = make_float2(cac.x, gs * dx * dy);      // (CA, CB)
+            gr[2] = make_float2(cac.y, dal * G);           // (CC, O)
+            // (a dx + b dy, b dx + c dy)
+            const float2 m = __ffma2_rn(make_float2(a.z, a.w), make_float2(dx, dx),
+                                        __fmul2_rn(make_float2(a.w, b.x), make_float2(dy, dy)));
+            gu += gs * m.x;
+            gv += gs * m.y;
           }
-          gr[R_U] = gu;
-          gr[R_V] = gv;
+          gr[0] = make_float2(gu, gv);
         }
       }
       if (__any_sync(kFull, contrib)) {
@@ -440,8 +457,9 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
 }
 
 // Persistent kernels: every warp pulls work items (tile, 8x4 block) from an
-// atomic counter until the frame is done, so no warp waits for another and the
-// tail is one small item.  The result does not depend on which warp takes
+// atomic counter until the frame is done, so no warp waits for another.  Items
+// come in the binning's work order (tiles with the longest lists first), so the
+// last items handed out are short and the tail is small.  The result does not depend on which warp takes
 // which item (each pixel is computed by exactly one warp).
 constexpr int kRenderThreads = 256;
 
@@ -453,6 +471,7 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
   Header* hdr = at<Header>(ws, L.hdr);
   if (hdr->status == GS_ERR_CAPACITY) return;
   float4 (*buf)[4][32] = s_rec[threadIdx.x >> 5];
+  const int* order = at<int>(ws, L.tile_order);
   const int lane = threadIdx.x & 31;
   uint32_t evals = 0;
   for (;;) {
@@ -460,7 +479,7 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     if (lane == 0) item = atomicAdd(&hdr->work_fwd, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= n_items) break;
-    fwd_item<LOSS, GEO>(fd, ws, L, maps, item / subs, item % subs, buf, evals);
+    fwd_item<LOSS, GEO>(fd, ws, L, maps, order[item / subs], item % subs, buf, evals);
     __syncwarp();
   }
   count_evals(evals, &hdr->n_evals_fwd);
@@ -476,6 +495,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
   if (hdr->status == GS_ERR_CAPACITY) return;
   float4 (*my)[32] = s_rec[threadIdx.x >> 5];
   uint32_t* my_e = s_ent[threadIdx.x >> 5];
+  const int* order = at<int>(ws, L.tile_order);
   const int lane = threadIdx.x & 31;
   uint32_t evals = 0;
   for (;;) {
@@ -483,7 +503,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     if (lane == 0) item = atomicAdd(&hdr->work_bwd, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= n_items) break;
-    bwd_item<LOSS>(fd, ws, L, g, item / subs, item % subs, my, my_e, evals);
+    bwd_item<LOSS>(fd, ws, L, g, order[item / subs], item % subs, my, my_e, evals);
     __syncwarp();
   }
   count_evals(evals, &hdr->n_evals_bwd);

@@ -127,6 +127,7 @@ struct Layout {
   size_t ptile_final, pval_final;  // where the sorted pairs end up
   size_t hist, htot;        // radix histograms [256][nb], digit totals [256]
   size_t ranges;            // [T] int2
+  size_t tile_order;        // [T] int: compositing work order (heaviest tiles first)
   size_t px_T, px_last, px_med;
   size_t grad2d;            // [E][16] float
   size_t px_loss;           // [kLossPlanes][NPIX] float when losses, else 0 bytes
