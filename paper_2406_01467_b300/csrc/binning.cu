@@ -419,31 +419,43 @@ k_ranges(const uint32_t* __restrict__ ptile, const unsigned long long* n_pairs_p
   }
 }
 
-// Work order of the compositing kernels: tiles by decreasing list length
-// (buckets of equal floor(log2(length)), heaviest bucket first), so that the
-// longest items start first and the persistent kernels end on short ones.  One
-// block; the order inside a bucket is arbitrary (each pixel is computed by one
-// warp whatever the order).
-__global__ void __launch_bounds__(1024) k_tile_order(const int2* __restrict__ ranges, int T, int* __restrict__ order) {
-  __shared__ int cnt[32], off[32];
-  if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
+// Work order of the compositing kernels: tiles by decreasing cost, so that
+// the longest items start first and the persistent kernels end on short ones.
+// The cost (the tile's list length unless `cost` is given) is bucketed by its
+// floor(log2) and three more mantissa bits (256 buckets, heaviest first); one
+// block, counting sort in shared memory.  The order inside a bucket is arbitrary: each pixel is
+// computed by one warp whatever the order.
+__device__ inline int cost_bucket(uint32_t c) {
+  if (c < 8) return (int)c;
+  const int e = 31 - __clz(c);                      // >= 3
+  return ((e - 2) << 3) | (int)((c >> (e - 3)) & 7u);   // monotone in c, < 256
+}
+
+__global__ void __launch_bounds__(1024) k_tile_order(const int2* __restrict__ ranges,
+                                                     const uint32_t* __restrict__ cost, int T,
+                                                     int* __restrict__ order) {
+  __shared__ int cnt[256];
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) cnt[b] = 0;
   __syncthreads();
   for (int t = threadIdx.x; t < T; t += blockDim.x) {
-    const int2 r = ranges[t];
-    const int len = r.y - r.x;
-    atomicAdd(&cnt[len > 0 ? 31 - __clz(len) : 0], 1);
+    const uint32_t c = cost ? cost[t] : (uint32_t)max(ranges[t].y - ranges[t].x, 0);
+    atomicAdd(&cnt[cost_bucket(c)], 1);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {   // exclusive offsets, heaviest bucket first
     int acc = 0;
-    for (int b = 31; b >= 0; --b) { off[b] = acc; acc += cnt[b]; }
+    for (int b = 255; b >= 0; --b) { const int n = cnt[b]; cnt[b] = acc; acc += n; }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < T; t += blockDim.x) {
-    const int2 r = ranges[t];
-    const int len = r.y - r.x;
-    order[atomicAdd(&off[len > 0 ? 31 - __clz(len) : 0], 1)] = t;
+    const uint32_t c = cost ? cost[t] : (uint32_t)max(ranges[t].y - ranges[t].x, 0);
+    order[atomicAdd(&cnt[cost_bucket(c)], 1)] = t;
   }
+}
+
+cudaError_t launch_tile_order(void* ws, const Layout& L, const uint32_t* cost, int* order, cudaStream_t s) {
+  if (L.T > 0) k_tile_order<<<1, 1024, 0, s>>>(at<int2>(ws, L.ranges), cost, (int)L.T, order);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -506,9 +518,8 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   cudaMemsetAsync(at<int2>(ws, L.ranges), 0, sizeof(int2) * (size_t)L.T, s);
   int g = (int)std::min<int64_t>((L.Pcap + 255) / 256, 148 * 32);
   k_ranges<<<g, 256, 0, s>>>(ptile, &hdr->n_pairs, L.Pcap, at<int2>(ws, L.ranges));
-  // 7. compositing work order
-  if (L.T > 0) k_tile_order<<<1, 1024, 0, s>>>(at<int2>(ws, L.ranges), (int)L.T, at<int>(ws, L.tile_order));
-  return cudaGetLastError();
+  // 7. compositing work order (by list length)
+  return launch_tile_order(ws, L, nullptr, at<int>(ws, L.tile_order), s);
 }
 
 }  // namespace gs
