@@ -27,8 +27,8 @@
 // Backward replays each pixel from its last contributor toward the front,
 // recovering T by division (alpha <= alpha_max < 1) and the colour / normal
 // "behind" sums recursively; nothing per (pixel, splat) is stored.  Each warp
-// reduces the 15 per-splat gradients of its 32 pixels with a transposed
-// reduce-scatter (16 shuffles instead of 75) and issues one vector of atomics.
+// reduces the 15 per-splat gradients of its 32 pixels with a reduce-scatter
+// through shared memory and issues one vector of atomics.
 // Eq. 23 with constant weights adds dL/dd_k = 4 w_k W (d_k - mean) to each
 // contributor's planar depth; Eq. 24 enters through the map gradients of
 // alpha, normal and depth that the normal-consistency backward stored.
@@ -257,42 +257,31 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   }
 }
 
-// Transposed warp reduce-scatter of 16 values held as 8 pairs (v[k] = slots
-// 2k, 2k+1): afterwards lane l holds the warp-wide sum of slot (l >> 1)
-// (lanes l and l^1 hold the same value).  The additions are packed FP32x2.
-__device__ inline float warp_reduce_scatter16(float2 (&v)[8]) {
+// Warp reduce-scatter of 16 values held as 8 pairs (v[k] = slots 2k, 2k+1)
+// through the warp's shared scratch red[16][kRedStride]: every lane stores its
+// 16 values (red[slot][lane]), then lane l adds slot l >> 1 over one half of
+// the warp with four 16-byte loads and lanes l, l^1 combine their halves.
+// Afterwards lane l holds the warp-wide sum of slot (l >> 1).  The row stride
+// of 36 floats keeps both the stores and the 16-byte loads free of bank
+// conflicts.
+constexpr int kRedStride = 36;
+
+__device__ inline float warp_reduce_scatter16(const float2 (&v)[8], float* __restrict__ red) {
   const int lane = threadIdx.x & 31;
-  {
-    const bool hi = lane & 16;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {   // slots 2k, 2k+1 vs 2k+8, 2k+9
-      const float2 send = hi ? v[k] : v[k + 4];
-      const float2 keep = hi ? v[k + 4] : v[k];
-      const float2 recv = make_float2(__shfl_xor_sync(kFull, send.x, 16), __shfl_xor_sync(kFull, send.y, 16));
-      v[k] = __fadd2_rn(keep, recv);
-    }
+  for (int k = 0; k < 8; ++k) {
+    red[(2 * k) * kRedStride + lane] = v[k].x;
+    red[(2 * k + 1) * kRedStride + lane] = v[k].y;
   }
-  {
-    const bool hi = lane & 8;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const float2 send = hi ? v[k] : v[k + 2];
-      const float2 keep = hi ? v[k + 2] : v[k];
-      const float2 recv = make_float2(__shfl_xor_sync(kFull, send.x, 8), __shfl_xor_sync(kFull, send.y, 8));
-      v[k] = __fadd2_rn(keep, recv);
-    }
-  }
-  {
-    const bool hi = lane & 4;
-    const float2 send = hi ? v[0] : v[1];
-    const float2 keep = hi ? v[1] : v[0];
-    const float2 recv = make_float2(__shfl_xor_sync(kFull, send.x, 4), __shfl_xor_sync(kFull, send.y, 4));
-    v[0] = __fadd2_rn(keep, recv);
-  }
-  const bool hi = lane & 2;
-  const float send = hi ? v[0].x : v[0].y;
-  const float keep = hi ? v[0].y : v[0].x;
-  const float r = keep + __shfl_xor_sync(kFull, send, 2);
+  __syncwarp();
+  const float4* row = reinterpret_cast<const float4*>(red + (lane >> 1) * kRedStride + (lane & 1) * 16);
+  const float4 a = row[0], b = row[1], c = row[2], d = row[3];
+  float2 acc = __fadd2_rn(make_float2(a.x, a.y), make_float2(a.z, a.w));
+  acc = __fadd2_rn(acc, __fadd2_rn(make_float2(b.x, b.y), make_float2(b.z, b.w)));
+  acc = __fadd2_rn(acc, __fadd2_rn(make_float2(c.x, c.y), make_float2(c.z, c.w)));
+  acc = __fadd2_rn(acc, __fadd2_rn(make_float2(d.x, d.y), make_float2(d.z, d.w)));
+  __syncwarp();   // the scratch is rewritten by the next call
+  const float r = acc.x + acc.y;
   return r + __shfl_xor_sync(kFull, r, 1);
 }
 
@@ -301,6 +290,7 @@ __device__ inline float warp_reduce_scatter16(float2 (&v)[8]) {
 template <bool LOSS>
 __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restrict__ ws, const Layout& L,
                                 const gs_map_grads& g, int tile, int sub, float4 (*my)[32], uint32_t* my_e,
+                                float* my_red,
                                 uint32_t& evals) {
   const TileCtx c = tile_ctx(fd, tile, sub);
   const int2 range = at<int2>(ws, L.ranges)[tile];
@@ -446,7 +436,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
         }
       }
       if (__any_sync(kFull, contrib)) {
-        const float s = warp_reduce_scatter16(gr);
+        const float s = warp_reduce_scatter16(gr, my_red);
         const int slot = lane >> 1;
         if ((lane & 1) == 0 && slot != R_CUT && s != 0.f)
           atomicAdd(grad + (int64_t)my_e[j] * kRecFloats + slot, s);
@@ -491,6 +481,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
              int n_items) {
   __shared__ float4 s_rec[kRenderThreads / 32][4][32];
   __shared__ uint32_t s_ent[kRenderThreads / 32][32];
+  __shared__ __align__(16) float s_red[kRenderThreads / 32][16 * kRedStride];
   Header* hdr = at<Header>(ws, L.hdr);
   if (hdr->status == GS_ERR_CAPACITY) return;
   float4 (*my)[32] = s_rec[threadIdx.x >> 5];
@@ -503,7 +494,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     if (lane == 0) item = atomicAdd(&hdr->work_bwd, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= n_items) break;
-    bwd_item<LOSS>(fd, ws, L, g, order[item / subs], item % subs, my, my_e, evals);
+    bwd_item<LOSS>(fd, ws, L, g, order[item / subs], item % subs, my, my_e, s_red[threadIdx.x >> 5], evals);
     __syncwarp();
   }
   count_evals(evals, &hdr->n_evals_bwd);
