@@ -172,8 +172,8 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   const int passes = (tile_sort_bits(T) + kRadixBits - 1) / kRadixBits;
   L.ptile_final = L.ptile[passes & 1];
   L.pval_final = L.pval[passes & 1];
-  L.hist = take(4 * (size_t)kRadix * nbmax);
-  L.htot = take(4 * (size_t)kRadix);
+  L.sortaux_bytes = 8192 + (size_t)4 * nbmax * kRadix * 8;   // histograms + tickets, 4 passes of look-back
+  L.sortaux = take(L.sortaux_bytes);
   L.ranges = take(8 * (size_t)T);
   L.tile_order = take(4 * (size_t)T);
   const bool bwd_state = !p.geometry_only;   // per-pixel replay state and 2D gradients

@@ -12,8 +12,9 @@
 //      list is then in (depth, entry) order, the same order as a full sort on
 //      (tile, depth bits, entry) keys;
 //   6. [start, end) of each tile.
-// Each radix pass is reduce-then-scan (histogram, per-digit scan, stable
-// scatter); no kernel waits on another block.
+// The radix sort is one-sweep: one histogram kernel for all passes, then one
+// kernel per pass whose blocks chain their digit offsets by decoupled look-back
+// (bounded waits).
 #include <algorithm>
 
 #include "gs_internal.cuh"
@@ -279,134 +280,6 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
 // ---------------------------------------------------------------------------
 // Radix sort pass: histogram, per-digit scan over blocks, stable scatter
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSortThreads)
-k_radix_hist(const uint32_t* __restrict__ kin, const unsigned long long* count_ptr, int64_t cap,
-             int shift, uint32_t* __restrict__ hist, int nb) {
-  __shared__ uint32_t s_h[8][kRadix];
-  const int w = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&s_h[0][0])[i] = 0;
-  __syncthreads();
-  const int64_t n = clamp_count(count_ptr, cap);
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  if (base < n) {
-    int d[kSortItems];
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {   // all loads in flight before any ranking
-      const int64_t i = WarpItems::index(base, r);
-      d[r] = i < n ? (int)((__ldg(kin + i) >> shift) & (kRadix - 1)) : kRadix;
-    }
-    const unsigned lt = lanemask_lt();
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-      const unsigned peers = __match_any_sync(FULL, d[r]);
-      if (d[r] < kRadix && (peers & lt) == 0) s_h[w][d[r]] += __popc(peers);
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  const int dg = threadIdx.x;
-  uint32_t s = 0;
-  for (int i = 0; i < 8; ++i) s += s_h[i][dg];
-  hist[(int64_t)dg * nb + blockIdx.x] = s;
-}
-
-// Block d scans hist[d][0..nb) (exclusive, in place) and writes the digit total.
-__global__ void __launch_bounds__(kSortThreads)
-k_radix_scan(uint32_t* __restrict__ hist, int nb, uint32_t* __restrict__ tot) {
-  __shared__ uint32_t s_warp[33];
-  uint32_t* h = hist + (int64_t)blockIdx.x * nb;
-  const int per = (nb + kSortThreads - 1) / kSortThreads;
-  const int b0 = threadIdx.x * per;
-  uint32_t sum = 0;
-  for (int i = 0; i < per; ++i)
-    if (b0 + i < nb) sum += h[b0 + i];
-  uint32_t total;
-  uint32_t off = block_exclusive_scan(sum, s_warp, &total);
-  for (int i = 0; i < per; ++i)
-    if (b0 + i < nb) {
-      uint32_t v = h[b0 + i];
-      h[b0 + i] = off;
-      off += v;
-    }
-  if (threadIdx.x == 0) tot[blockIdx.x] = total;
-}
-
-__global__ void __launch_bounds__(kSortThreads)
-k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                const unsigned long long* count_ptr, int64_t cap, int shift,
-                const uint32_t* __restrict__ hist, const uint32_t* __restrict__ tot, int nb) {
-  __shared__ uint32_t s_wcnt[kRadix][8];
-  __shared__ uint32_t s_keys[kSortTile];
-  __shared__ uint32_t s_vals[kSortTile];
-  __shared__ uint32_t s_dstart[kRadix];
-  __shared__ uint32_t s_gbase[kRadix];
-  __shared__ uint32_t s_warp[33];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t n = clamp_count(count_ptr, cap);
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  if (base >= n) return;
-  for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
-  // global start of each digit for this block
-  {
-    const int d = threadIdx.x;
-    uint32_t t = tot[d];
-    uint32_t dbase = block_exclusive_scan(t, s_warp, nullptr);
-    s_gbase[d] = dbase + hist[(int64_t)d * nb + blockIdx.x];
-  }
-  __syncthreads();
-  uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
-  const unsigned lt = lanemask_lt();
-#pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {   // all loads in flight before any ranking
-    const int64_t i = WarpItems::index(base, r);
-    k[r] = i < n ? __ldg(kin + i) : 0u;
-    v[r] = i < n ? __ldg(vin + i) : 0u;
-  }
-#pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    const bool ok = WarpItems::index(base, r) < n;
-    int d = ok ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
-    unsigned peers = __match_any_sync(FULL, d);
-    uint32_t old = d < kRadix ? s_wcnt[d][w] : 0u;
-    rank[r] = old + __popc(peers & lt);
-    __syncwarp();
-    if (d < kRadix && (peers & lt) == 0) s_wcnt[d][w] = old + __popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
-  // block-local exclusive scan over (digit, warp) in digit-major order
-  {
-    const int d = threadIdx.x;
-    uint32_t c[8], s = 0;
-    for (int i = 0; i < 8; ++i) { c[i] = s_wcnt[d][i]; s += c[i]; }
-    uint32_t start = block_exclusive_scan(s, s_warp, nullptr);
-    s_dstart[d] = start;
-    uint32_t run = start;
-    for (int i = 0; i < 8; ++i) { s_wcnt[d][i] = run; run += c[i]; }
-  }
-  __syncthreads();
-  for (int r = 0; r < kSortItems; ++r) {
-    int64_t i = WarpItems::index(base, r);
-    if (i < n) {
-      int d = (int)((k[r] >> shift) & (kRadix - 1));
-      uint32_t pos = s_wcnt[d][w] + rank[r];
-      s_keys[pos] = k[r];
-      s_vals[pos] = v[r];
-    }
-  }
-  __syncthreads();
-  const int nloc = (int)min((int64_t)kSortTile, n - base);
-  for (int i = threadIdx.x; i < nloc; i += kSortThreads) {
-    uint32_t kk = s_keys[i];
-    int d = (int)((kk >> shift) & (kRadix - 1));
-    uint32_t dst = s_gbase[d] + (uint32_t)i - s_dstart[d];
-    kout[dst] = kk;
-    vout[dst] = s_vals[i];
-  }
-  (void)lane;
-}
-
 __global__ void __launch_bounds__(256)
 k_ranges(const uint32_t* __restrict__ ptile, const unsigned long long* n_pairs_ptr, int64_t cap,
          int2* __restrict__ ranges) {
@@ -459,14 +332,160 @@ cudaError_t launch_tile_order(void* ws, const Layout& L, const uint32_t* cost, i
 }
 
 // ---------------------------------------------------------------------------
+// One-sweep LSD radix sort: the digit histograms of every pass come from one
+// read of the keys (k_digit_hist); each pass is then a single kernel in which
+// a block ranks its 4096 keys, publishes its per-digit counts, finds the
+// counts of all blocks before it by decoupled look-back (each predecessor's
+// word holds its own count, flagged A, or the inclusive prefix, flagged P) and
+// scatters.  Blocks take their tile of keys in the order they start (a ticket
+// counter), so a block only ever waits for blocks that are already running;
+// every wait is bounded and sets GS_ERR_TIMEOUT if it runs out.
+// ---------------------------------------------------------------------------
+constexpr int kMaxPasses = 4;
+constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62, kFlagMask = 3ull << 62;
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ inline void st_relaxed(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ inline unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_digit_hist(const uint32_t* __restrict__ kin, const unsigned long long* count_ptr, int64_t cap, int passes,
+             uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t s_h[kMaxPasses][kRadix];
+  for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kSortThreads) (&s_h[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t n = clamp_count(count_ptr, cap);
+  const unsigned lt = lanemask_lt();
+  const int64_t step = (int64_t)gridDim.x * kSortThreads;
+  for (int64_t i0 = (int64_t)blockIdx.x * kSortThreads; i0 < n; i0 += step) {   // warp-uniform loop
+    const int64_t i = i0 + threadIdx.x;
+    const uint32_t k = i < n ? __ldg(kin + i) : 0u;
+    for (int p = 0; p < passes; ++p) {
+      const int d = i < n ? (int)((k >> (kRadixBits * p)) & (kRadix - 1)) : kRadix;
+      const unsigned peers = __match_any_sync(FULL, d);
+      if (d < kRadix && (peers & lt) == 0) atomicAdd(&s_h[p][d], __popc(peers));
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) {
+    const uint32_t c = (&s_h[0][0])[i];
+    if (c) atomicAdd(ghist + i, c);
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+           uint32_t* __restrict__ vout, const unsigned long long* count_ptr, int64_t cap, int pass,
+           const uint32_t* __restrict__ ghist, unsigned long long* __restrict__ look, int* ticket, Header* hdr) {
+  __shared__ uint32_t s_wcnt[kRadix][8];
+  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_dstart[kRadix];
+  __shared__ uint32_t s_gbase[kRadix];
+  __shared__ uint32_t s_warp[33];
+  __shared__ int s_blk;
+  const int w = threadIdx.x >> 5;
+  const int shift = kRadixBits * pass;
+  if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1);
+  for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
+  __syncthreads();
+  const int blk = s_blk;
+  const int64_t n = clamp_count(count_ptr, cap);
+  const int64_t base = (int64_t)blk * kSortTile;
+  if (base >= n) return;   // so do all blocks with later tickets: nobody waits for this one
+  uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {   // all loads in flight before any ranking
+    const int64_t i = WarpItems::index(base, r);
+    k[r] = i < n ? __ldg(kin + i) : 0u;
+    v[r] = i < n ? __ldg(vin + i) : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const bool ok = WarpItems::index(base, r) < n;
+    const int d = ok ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
+    const unsigned peers = __match_any_sync(FULL, d);
+    const uint32_t old = d < kRadix ? s_wcnt[d][w] : 0u;
+    rank[r] = old + __popc(peers & lt);
+    __syncwarp();
+    if (d < kRadix && (peers & lt) == 0) s_wcnt[d][w] = old + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  const int d = threadIdx.x;   // one thread per digit from here on
+  uint32_t c[8], cnt = 0;
+  for (int i = 0; i < 8; ++i) { c[i] = s_wcnt[d][i]; cnt += c[i]; }
+  unsigned long long* mine = look + (int64_t)blk * kRadix + d;
+  st_relaxed(mine, (blk == 0 ? kFlagP : kFlagA) | cnt);   // successors may start looking
+  // block-local exclusive scan over (digit, warp) in digit-major order, and the
+  // digit's start in the whole key set (exclusive scan of the global histogram)
+  const uint32_t start = block_exclusive_scan(cnt, s_warp, nullptr);
+  const uint32_t dbase = block_exclusive_scan(ghist[pass * kRadix + d], s_warp, nullptr);
+  s_dstart[d] = start;
+  uint32_t run = start;
+  for (int i = 0; i < 8; ++i) { s_wcnt[d][i] = run; run += c[i]; }
+  // decoupled look-back: keys of digit d in the blocks before this one
+  uint32_t excl = 0;
+  if (blk > 0) {
+    int j = blk - 1, spins = 0;
+    for (;;) {
+      const unsigned long long f = ld_relaxed(look + (int64_t)j * kRadix + d);
+      const unsigned long long st = f & kFlagMask;
+      if (st == 0) {
+        if (++spins > kSpinLimit) { set_status(hdr, GS_ERR_TIMEOUT); break; }
+        continue;
+      }
+      excl += (uint32_t)f;
+      if (st == kFlagP || j == 0) break;
+      --j;
+    }
+    st_relaxed(mine, kFlagP | (excl + cnt));
+  }
+  s_gbase[d] = dbase + excl;
+  __syncthreads();
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t i = WarpItems::index(base, r);
+    if (i < n) {
+      const int dd = (int)((k[r] >> shift) & (kRadix - 1));
+      const uint32_t pos = s_wcnt[dd][w] + rank[r];
+      s_keys[pos] = k[r];
+      s_vals[pos] = v[r];
+    }
+  }
+  __syncthreads();
+  const int nloc = (int)min((int64_t)kSortTile, n - base);
+  for (int i = threadIdx.x; i < nloc; i += kSortThreads) {
+    const uint32_t kk = s_keys[i];
+    const int dd = (int)((kk >> shift) & (kRadix - 1));
+    const uint32_t dst = s_gbase[dd] + (uint32_t)i - s_dstart[dd];
+    kout[dst] = kk;
+    vout[dst] = s_vals[i];
+  }
+}
+
+// Sorts (k0, v0) by the low `bits` bits of the keys; the result ends in
+// (k0, v0) after an even number of 8-bit passes, else in (k1, v1).
 static cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                              const unsigned long long* count, int64_t cap, int nb, int bits,
-                              uint32_t* hist, uint32_t* tot, cudaStream_t s) {
+                              const unsigned long long* count, int64_t cap, int nb, int bits, void* aux,
+                              size_t aux_bytes, Header* hdr, cudaStream_t s) {
+  const int passes = (bits + kRadixBits - 1) / kRadixBits;
+  uint32_t* ghist = static_cast<uint32_t*>(aux);                       // [kMaxPasses][256]
+  int* tickets = reinterpret_cast<int*>(ghist + kMaxPasses * kRadix);   // [kMaxPasses]
+  unsigned long long* look = reinterpret_cast<unsigned long long*>(static_cast<char*>(aux) + 8192);
+  cudaError_t e = cudaMemsetAsync(aux, 0, std::min(aux_bytes, (size_t)8192 + (size_t)passes * nb * kRadix * 8), s);
+  if (e != cudaSuccess) return e;
+  k_digit_hist<<<std::min(nb, 148 * 8), kSortThreads, 0, s>>>(k0, count, cap, passes, ghist);
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
-  for (int shift = 0; shift < bits; shift += kRadixBits) {
-    k_radix_hist<<<nb, kSortThreads, 0, s>>>(ki, count, cap, shift, hist, nb);
-    k_radix_scan<<<kRadix, kSortThreads, 0, s>>>(hist, nb, tot);
-    k_radix_scatter<<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, cap, shift, hist, tot, nb);
+  for (int p = 0; p < passes; ++p) {
+    k_onesweep<<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, cap, p, ghist, look + (int64_t)p * nb * kRadix,
+                                           tickets + p, hdr);
     uint32_t* t;
     t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
@@ -486,8 +505,6 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   uint32_t* key = at<uint32_t>(ws, L.key);
   uint32_t* touched = at<uint32_t>(ws, L.touched);
   uint32_t* blk = at<uint32_t>(ws, L.blk);
-  uint32_t* hist = at<uint32_t>(ws, L.hist);
-  uint32_t* tot = at<uint32_t>(ws, L.htot);
   uint32_t *vk0 = at<uint32_t>(ws, L.vkey[0]), *vk1 = at<uint32_t>(ws, L.vkey[1]);
   uint32_t *vv0 = at<uint32_t>(ws, L.vval[0]), *vv1 = at<uint32_t>(ws, L.vval[1]);
   uint32_t *pt0 = at<uint32_t>(ws, L.ptile[0]), *pt1 = at<uint32_t>(ws, L.ptile[1]);
@@ -498,7 +515,8 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   k_scan_partials<<<1, 1024, 0, s>>>(blk, L.nb_E, &hdr->n_vis, 0, hdr);
   k_compact<<<L.nb_E, kSortThreads, 0, s>>>(key, L.E, blk, vk0, vv0);
   // 2. depth sort: 31 bits (z > 0, so the sign bit is clear)
-  cudaError_t err = radix_sort(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, hist, tot, s);
+  void* aux = at<void>(ws, L.sortaux);
+  cudaError_t err = radix_sort(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, aux, L.sortaux_bytes, hdr, s);
   if (err != cudaSuccess) return err;
   // 3. pair offsets
   k_block_sums<1><<<L.nb_E, kSortThreads, 0, s>>>(touched, vv0, &hdr->n_vis, L.E, blk);
@@ -511,7 +529,7 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
                                      pair_off, L.Pcap, pt0, pv0);
   // 5. tile sort
   const int bits = tile_sort_bits(L.T);
-  err = radix_sort(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, hist, tot, s);
+  err = radix_sort(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, aux, L.sortaux_bytes, hdr, s);
   if (err != cudaSuccess) return err;
   uint32_t* ptile = at<uint32_t>(ws, L.ptile_final);
   // 6. ranges

@@ -125,7 +125,8 @@ struct Layout {
   size_t blk;               // per-block partials of the scans
   size_t ptile[2], pval[2]; // pair sort ping-pong
   size_t ptile_final, pval_final;  // where the sorted pairs end up
-  size_t hist, htot;        // radix histograms [256][nb], digit totals [256]
+  size_t sortaux;           // radix sort: digit histograms, tickets, look-back words
+  size_t sortaux_bytes;
   size_t ranges;            // [T] int2
   size_t tile_order;        // [T] int: compositing work order (heaviest tiles first)
   size_t px_T, px_last, px_med;
