@@ -451,30 +451,39 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
   const uint32_t* key = at<uint32_t>(ws, L.key);
   const float4* g2d = at<float4>(ws, L.grad2d);
   const float lp = fd->lowpass;
+  // Single-view scenes store their gradients through shared memory: each thread
+  // writes its rows there, then the block writes the chunk's contiguous
+  // gradient ranges with coalesced stores (the SH rows as 16-byte pieces).
+  constexpr int R4 = (3 * K) / 4;                  // float4s of one SH row
+  constexpr bool STAGE_SH = (3 * K) % 4 == 0;
+  constexpr int R4P = STAGE_SH ? (R4 | 1) : 1;     // odd row stride: no bank conflicts
+  __shared__ float4 s_sh[kPreThreads * R4P];
+  __shared__ float s_m[3 * kPreThreads], s_s[3 * kPreThreads], s_o[kPreThreads];
+  __shared__ float4 s_q[kPreThreads];
   for (int bi = blockIdx.x; bi < fd->n_chunks; bi += gridDim.x) {
     const Chunk ch = chunk_of(fd, bi);
     const ViewDev& V = fd->views[ch.view];
     const SceneDev& S = fd->scenes[V.scene];
     if (S.dtype != dtype_code<T>() || S.sh_degree != D || (S.filter_var != nullptr) != FILT) continue;
     const int t = threadIdx.x;
-    if (t >= ch.n) continue;
+    const bool act = t < ch.n;
     const gs_scene_grads& Dg = gp.g[V.scene];
     const bool store = S.n_views == 1;  // else the buffers were zeroed and we add
+    const bool stage_sh = STAGE_SH && store && Dg.dsh &&
+                          (reinterpret_cast<uintptr_t>(Dg.dsh) & 15) == 0;   // block-uniform
     auto put = [&](float* dst, int64_t i, float v) {
       if (store) dst[i] = v;
       else if (v != 0.f) atomicAdd(dst + i, v);
     };
-    const int64_t e = ch.e0 + t, g = ch.g0 + t;
+    const int64_t e = ch.e0 + (act ? t : 0), g = ch.g0 + (act ? t : 0);
     float gm[3] = {0.f, 0.f, 0.f}, gsc[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, go = 0.f;
-    if (key[e] == kInvalidKey) {
-      if (store && Dg.dsh) {
-        float* dst = Dg.dsh + 3 * K * g;
-        if ((3 * K) % 4 == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+    if (!act || key[e] == kInvalidKey) {
+      if (stage_sh) {
 #pragma unroll
-          for (int f = 0; f < 3 * K / 4; ++f) reinterpret_cast<float4*>(dst)[f] = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else {
-          for (int j = 0; j < 3 * K; ++j) dst[j] = 0.f;
-        }
+        for (int f = 0; f < R4; ++f) s_sh[t * R4P + f] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else if (act && store && Dg.dsh) {
+        float* dst = Dg.dsh + 3 * K * g;
+        for (int j = 0; j < 3 * K; ++j) dst[j] = 0.f;
       }
     } else {
       float m[3], s[3], q[4], o;
@@ -519,17 +528,17 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
         float dd = dir[0] * gdir[0] + dir[1] * gdir[1] + dir[2] * gdir[2];
         for (int k = 0; k < 3; ++k) gm[k] += (gdir[k] - dir[k] * dd) * il;
         // dL/dc_jk = Y_j gval_k
-        if (Dg.dsh) {
+        if (stage_sh) {
+#pragma unroll
+          for (int f = 0; f < R4; ++f) {
+            float v4[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v4[c] = Y[(4 * f + c) / 3] * gval[(4 * f + c) % 3];
+            s_sh[t * R4P + f] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+          }
+        } else if (Dg.dsh) {
           float* dst = Dg.dsh + 3 * K * g;
-          if (store && (3 * K) % 4 == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-#pragma unroll
-            for (int f = 0; f < 3 * K / 4; ++f) {
-              float v4[4];
-#pragma unroll
-              for (int c = 0; c < 4; ++c) v4[c] = Y[(4 * f + c) / 3] * gval[(4 * f + c) % 3];
-              reinterpret_cast<float4*>(dst)[f] = make_float4(v4[0], v4[1], v4[2], v4[3]);
-            }
-          } else {
+          {
 #pragma unroll
             for (int j = 0; j < K; ++j)
 #pragma unroll
@@ -644,10 +653,30 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
         go *= rp;
       }
     }
-    if (Dg.dmeans) for (int k = 0; k < 3; ++k) put(Dg.dmeans, 3 * g + k, gm[k]);
-    if (Dg.dscales) for (int k = 0; k < 3; ++k) put(Dg.dscales, 3 * g + k, gsc[k]);
-    if (Dg.dquats) for (int k = 0; k < 4; ++k) put(Dg.dquats, 4 * g + k, gq[k]);
-    if (Dg.dopacities) put(Dg.dopacities, g, go);
+    if (store) {
+      for (int k = 0; k < 3; ++k) { s_m[3 * t + k] = gm[k]; s_s[3 * t + k] = gsc[k]; }
+      s_q[t] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+      s_o[t] = go;
+      __syncthreads();
+      const int n = ch.n;
+      if (Dg.dmeans) for (int i = t; i < 3 * n; i += kPreThreads) Dg.dmeans[3 * ch.g0 + i] = s_m[i];
+      if (Dg.dscales) for (int i = t; i < 3 * n; i += kPreThreads) Dg.dscales[3 * ch.g0 + i] = s_s[i];
+      if (Dg.dquats)
+        for (int i = t; i < 4 * n; i += kPreThreads) Dg.dquats[4 * ch.g0 + i] = (&s_q[0].x)[i];
+      if (Dg.dopacities && act) Dg.dopacities[ch.g0 + t] = s_o[t];
+      if constexpr (STAGE_SH) {
+        if (stage_sh) {
+          float4* dst = reinterpret_cast<float4*>(Dg.dsh + 3 * K * ch.g0);
+          for (int f = t; f < R4 * n; f += kPreThreads) dst[f] = s_sh[(f / R4) * R4P + f % R4];
+        }
+      }
+      __syncthreads();   // the staging rows are rewritten by the next chunk
+    } else if (act) {
+      if (Dg.dmeans) for (int k = 0; k < 3; ++k) put(Dg.dmeans, 3 * g + k, gm[k]);
+      if (Dg.dscales) for (int k = 0; k < 3; ++k) put(Dg.dscales, 3 * g + k, gsc[k]);
+      if (Dg.dquats) for (int k = 0; k < 4; ++k) put(Dg.dquats, 4 * g + k, gq[k]);
+      if (Dg.dopacities) put(Dg.dopacities, g, go);
+    }
   }
 }
 
