@@ -157,8 +157,12 @@ def launches_per_step(n_tiles, n_dtypes=1):
     bits = max(1, int(np.ceil(np.log2(max(n_tiles, 2)))))
     tile_passes = (bits + 7) // 8
     setup, pre = 1, n_dtypes
-    binning = 3 + 4 * 3 + 2 + 2 + 3 * tile_passes + 1 + 1   # ... ranges, work order
-    return setup + pre + binning + 1 + 1 + n_dtypes
+    compaction = 3                    # block sums, scan of partials, compact
+    depth_sort = 1 + 4                # digit histogram + 4 one-sweep passes
+    pair_scan = 2 + 1 + 1             # block sums, scan of partials, pair offsets, emission
+    tile_sort = 1 + tile_passes       # digit histogram + one-sweep passes
+    binning = compaction + depth_sort + pair_scan + tile_sort + 1 + 1   # ranges, work order
+    return setup + pre + binning + 1 + 1 + n_dtypes   # render fwd, composite bwd, preprocess bwd
 
 
 # --------------------------------------------------------------------------------------
