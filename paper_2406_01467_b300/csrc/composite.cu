@@ -367,74 +367,61 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const int j = __ffs(m) - 1;
       m &= m - 1;
       const int idx = c1 - 1 - j;
+      // Branch-free: every lane evaluates the splat; lanes that do not blend it
+      // (behind their last contributor, or alpha below alpha_min) take alpha = 0,
+      // which leaves T and the running sums unchanged and zeroes every gradient.
       // gradient slots as pairs: (U,V) (CA,CB) (CC,O) (CUT,Z) (P0,P1) (N0,N1) (N2,R) (G,B)
       float2 gr[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) gr[k] = make_float2(0.f, 0.f);
-      bool contrib = false;
-      if (idx <= last) {
-        ++evals;
-        const float4 a = my[0][j], b = my[1][j];
-        const float2 d = __fadd2_rn(make_float2(a.x, a.y), nfp);     // (dx, dy)
-        const float dx = d.x, dy = d.y;
-        const float2 d2 = __fmul2_rn(d, d);                           // (dx^2, dy^2)
-        const float sig = 0.5f * (a.z * d2.x + b.x * d2.y) + a.w * dx * dy;
-        const float G = __expf(-sig);
-        const float raw = b.y * G;
-        const float al = fminf(amax, raw);
-        if (al >= amin) {
-          contrib = true;
-          const float4 e2 = my[2][j], e3 = my[3][j];
-          const float ia = __fdividef(1.f, 1.f - al);
-          T *= ia;                         // transmittance in front of this splat
-          const float w = al * T;
-          const float2 w2 = make_float2(w, w);
-          // colour and normal: (rgb, n) and the upstream (dC, dN) as three pairs
-          const float2 x0 = make_float2(e3.y, e3.z), x1 = make_float2(e3.w, e2.z), x2 = make_float2(e2.w, e3.x);
-          gr[5] = __fmul2_rn(w2, dN01);
-          gr[6] = __fmul2_rn(w2, dN2C0);
-          gr[7] = __fmul2_rn(w2, dC12);
-          // (x - S) enters both dL/dalpha and the update S += alpha (x - S)
-          const float2 q0 = __fadd2_rn(x0, make_float2(-S01.x, -S01.y));
-          const float2 q1 = __fadd2_rn(x1, make_float2(-S23.x, -S23.y));
-          const float2 q2 = __fadd2_rn(x2, make_float2(-S45.x, -S45.y));
-          float2 acc = __fmul2_rn(q0, U01);
-          acc = __ffma2_rn(q1, U23, acc);
-          acc = __ffma2_rn(q2, U45, acc);
-          const float2 al2 = make_float2(al, al);
-          S01 = __ffma2_rn(al2, q0, S01);
-          S23 = __ffma2_rn(al2, q1, S23);
-          S45 = __ffma2_rn(al2, q2, S45);
-          const float dal = T * (acc.x + acc.y) + dATf * ia;
-          float gu = 0.f, gv = 0.f;
-          if (LOSS) {                  // d = z_c + p . Delta (Eq. 4), median and Eq. 23
-            const float dk = b.w + e2.x * dx + e2.y * dy;
-            const float sd = c4 * w * (dk - dmean) + (idx == med ? dD : 0.f);
-            gr[3].y = sd;
-            gr[4] = __fmul2_rn(make_float2(sd, sd), d);
-            gu += sd * e2.x;
-            gv += sd * e2.y;
-          } else if (idx == med) {     // d = z_c + p . Delta (Eq. 4)
-            gr[3].y = dD;
-            gr[4] = __fmul2_rn(make_float2(dD, dD), d);
-            gu += dD * e2.x;
-            gv += dD * e2.y;
-          }
-          if (raw <= amax) {
-            const float gs = -dal * al;
-            const float2 hgs = make_float2(0.5f * gs, 0.5f * gs);
-            const float2 cac = __fmul2_rn(hgs, d2);        // (CA, CC)
-            gr[1] = make_float2(cac.x, gs * dx * dy);      // (CA, CB)
-            gr[2] = make_float2(cac.y, dal * G);           // (CC, O)
-            // (a dx + b dy, b dx + c dy)
-            const float2 m = __ffma2_rn(make_float2(a.z, a.w), make_float2(dx, dx),
-                                        __fmul2_rn(make_float2(a.w, b.x), make_float2(dy, dy)));
-            gu += gs * m.x;
-            gv += gs * m.y;
-          }
-          gr[0] = make_float2(gu, gv);
-        }
-      }
+      const bool live = idx <= last;
+      evals += live ? 1u : 0u;
+      const float4 a = my[0][j], b = my[1][j], e2 = my[2][j], e3 = my[3][j];
+      const float2 d = __fadd2_rn(make_float2(a.x, a.y), nfp);     // (dx, dy)
+      const float dx = d.x, dy = d.y;
+      const float2 d2 = __fmul2_rn(d, d);                           // (dx^2, dy^2)
+      const float sig = 0.5f * (a.z * d2.x + b.x * d2.y) + a.w * dx * dy;
+      const float G = __expf(-sig);
+      const float raw = b.y * G;
+      const float al0 = fminf(amax, raw);
+      const bool contrib = live && al0 >= amin;
+      const float al = contrib ? al0 : 0.f;
+      const float ia = __fdividef(1.f, 1.f - al);
+      T *= ia;                           // transmittance in front of this splat
+      const float w = al * T;
+      const float2 w2 = make_float2(w, w);
+      // colour and normal: (rgb, n) and the upstream (dC, dN) as three pairs
+      const float2 x0 = make_float2(e3.y, e3.z), x1 = make_float2(e3.w, e2.z), x2 = make_float2(e2.w, e3.x);
+      gr[5] = __fmul2_rn(w2, dN01);
+      gr[6] = __fmul2_rn(w2, dN2C0);
+      gr[7] = __fmul2_rn(w2, dC12);
+      // (x - S) enters both dL/dalpha and the update S += alpha (x - S)
+      const float2 q0 = __fadd2_rn(x0, make_float2(-S01.x, -S01.y));
+      const float2 q1 = __fadd2_rn(x1, make_float2(-S23.x, -S23.y));
+      const float2 q2 = __fadd2_rn(x2, make_float2(-S45.x, -S45.y));
+      float2 acc = __fmul2_rn(q0, U01);
+      acc = __ffma2_rn(q1, U23, acc);
+      acc = __ffma2_rn(q2, U45, acc);
+      const float2 al2 = make_float2(al, al);
+      S01 = __ffma2_rn(al2, q0, S01);
+      S23 = __ffma2_rn(al2, q1, S23);
+      S45 = __ffma2_rn(al2, q2, S45);
+      const float dal = contrib ? T * (acc.x + acc.y) + dATf * ia : 0.f;
+      // d = z_c + p . Delta (Eq. 4): the median splat, and Eq. 23 with the weights constant
+      float sd = (contrib && idx == med) ? dD : 0.f;
+      if (LOSS) sd += c4 * w * ((b.w + e2.x * dx + e2.y * dy) - dmean);
+      gr[3] = make_float2(0.f, sd);
+      gr[4] = __fmul2_rn(make_float2(sd, sd), d);
+      // alpha = o G below the clamp: opacity, conic and centre
+      const float gs = raw <= amax ? -dal * al : 0.f;
+      const float2 hgs = make_float2(0.5f * gs, 0.5f * gs);
+      const float2 cac = __fmul2_rn(hgs, d2);            // (CA, CC)
+      gr[1] = make_float2(cac.x, gs * dx * dy);          // (CA, CB)
+      gr[2] = make_float2(cac.y, raw <= amax ? dal * G : 0.f);   // (CC, O)
+      // (a dx + b dy, b dx + c dy)
+      const float2 mm = __ffma2_rn(make_float2(a.z, a.w), make_float2(dx, dx),
+                                   __fmul2_rn(make_float2(a.w, b.x), make_float2(dy, dy)));
+      const float2 guv = __ffma2_rn(make_float2(gs, gs), mm, __fmul2_rn(make_float2(sd, sd),
+                                                                          make_float2(e2.x, e2.y)));
+      gr[0] = guv;
       if (__any_sync(kFull, contrib)) {
         const float s = warp_reduce_scatter16(gr, my_red);
         const int slot = lane >> 1;
