@@ -53,24 +53,34 @@ __device__ inline void sh_basis(float x, float y, float z, float* Y) {
   Y[15] = -K3a * x * (x * x - 3.f * y * y);
 }
 
-// d Y_k / d (x, y, z) of the polynomials above.
-__device__ inline void sh_basis_grad(float x, float y, float z, float (*dY)[3]) {
-  dY[0][0] = 0.f; dY[0][1] = 0.f; dY[0][2] = 0.f;
-  dY[1][0] = 0.f; dY[1][1] = -K1; dY[1][2] = 0.f;
-  dY[2][0] = 0.f; dY[2][1] = 0.f; dY[2][2] = K1;
-  dY[3][0] = -K1; dY[3][1] = 0.f; dY[3][2] = 0.f;
-  dY[4][0] = K2a * y; dY[4][1] = K2a * x; dY[4][2] = 0.f;
-  dY[5][0] = 0.f; dY[5][1] = -K2a * z; dY[5][2] = -K2a * y;
-  dY[6][0] = 0.f; dY[6][1] = 0.f; dY[6][2] = 6.f * K2b * z;
-  dY[7][0] = -K2a * z; dY[7][1] = 0.f; dY[7][2] = -K2a * x;
-  dY[8][0] = 2.f * K2c * x; dY[8][1] = -2.f * K2c * y; dY[8][2] = 0.f;
-  dY[9][0] = -6.f * K3a * x * y; dY[9][1] = -K3a * (3.f * x * x - 3.f * y * y); dY[9][2] = 0.f;
-  dY[10][0] = K3b * y * z; dY[10][1] = K3b * x * z; dY[10][2] = K3b * x * y;
-  dY[11][0] = 0.f; dY[11][1] = -K3c * (5.f * z * z - 1.f); dY[11][2] = -10.f * K3c * y * z;
-  dY[12][0] = 0.f; dY[12][1] = 0.f; dY[12][2] = K3d * (15.f * z * z - 3.f);
-  dY[13][0] = -K3c * (5.f * z * z - 1.f); dY[13][1] = 0.f; dY[13][2] = -10.f * K3c * x * z;
-  dY[14][0] = 2.f * K3e * x * z; dY[14][1] = -2.f * K3e * y * z; dY[14][2] = K3e * (x * x - y * y);
-  dY[15][0] = -K3a * (3.f * x * x - 3.f * y * y); dY[15][1] = 6.f * K3a * x * y; dY[15][2] = 0.f;
+// (gx, gy, gz) = sum_k gY_k dY_k/d(x, y, z) for the first K polynomials above
+// (the transposed Jacobian of sh_basis applied to gY).
+template <int K>
+__device__ inline void sh_basis_vjp(float x, float y, float z, const float* gY, float* out) {
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  if (K > 1) {
+    gy -= K1 * gY[1];
+    gz += K1 * gY[2];
+    gx -= K1 * gY[3];
+  }
+  if (K > 4) {
+    gx += K2a * y * gY[4]; gy += K2a * x * gY[4];
+    gy -= K2a * z * gY[5]; gz -= K2a * y * gY[5];
+    gz += 6.f * K2b * z * gY[6];
+    gx -= K2a * z * gY[7]; gz -= K2a * x * gY[7];
+    gx += 2.f * K2c * x * gY[8]; gy -= 2.f * K2c * y * gY[8];
+  }
+  if (K > 9) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gx -= 6.f * K3a * x * y * gY[9]; gy -= K3a * (3.f * xx - 3.f * yy) * gY[9];
+    gx += K3b * y * z * gY[10]; gy += K3b * x * z * gY[10]; gz += K3b * x * y * gY[10];
+    gy -= K3c * (5.f * zz - 1.f) * gY[11]; gz -= 10.f * K3c * y * z * gY[11];
+    gz += K3d * (15.f * zz - 3.f) * gY[12];
+    gx -= K3c * (5.f * zz - 1.f) * gY[13]; gz -= 10.f * K3c * x * z * gY[13];
+    gx += 2.f * K3e * x * z * gY[14]; gy -= 2.f * K3e * y * z * gY[14]; gz += K3e * (xx - yy) * gY[14];
+    gx -= K3a * (3.f * xx - 3.f * yy) * gY[15]; gy += 6.f * K3a * x * y * gY[15];
+  }
+  out[0] = gx; out[1] = gy; out[2] = gz;
 }
 
 // Quantities of one entry that both passes need, in plain FP32 (any rounding).
@@ -450,6 +460,7 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
   constexpr int K = (D + 1) * (D + 1);
   const uint32_t* key = at<uint32_t>(ws, L.key);
   const float4* g2d = at<float4>(ws, L.grad2d);
+  const float4* rec4 = at<float4>(ws, L.rec);
   const float lp = fd->lowpass;
   // Single-view scenes store their gradients through shared memory: each thread
   // writes its rows there, then the block writes the chunk's contiguous
@@ -491,41 +502,27 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
       const float s0[3] = {s[0], s[1], s[2]};
       const float fv = FILT ? __ldg(S.filter_var + g) : 0.f;
       if (FILT) filter3d_apply(fv, s, o);   // s, o: filtered scales and opacity
-      float c[3 * K];
-      load_sh<T, K>(S, g, c);
-      Geo geo;
-      geo_forward(V, m, s, q, lp, geo);
-      const Geo& gg = geo;
-      const float4 ga = g2d[4 * e], gb4 = g2d[4 * e + 1], gc4 = g2d[4 * e + 2], gd4 = g2d[4 * e + 3];
-      const float gu = ga.x, gv = ga.y, gca = ga.z, gcb = ga.w;
-      const float gcc = gb4.x, gz = gb4.w;
-      go = gb4.y;
-      const float gp0 = gc4.x, gp1 = gc4.y, gn[3] = {gc4.z, gc4.w, gd4.x};
-      const float grgb[3] = {gd4.y, gd4.z, gd4.w};
-
-      // ---- colour: rgb = max(sum Y_j c_j + 1/2, 0) ----------------------------
+      // ---- colour first (its registers are free again before the geometry):
+      // rgb = max(sum_j Y_j c_j + 1/2, 0); a channel was clamped iff the forward
+      // record holds 0 for it
       {
-        float d[3] = {m[0] - V.campos[0], m[1] - V.campos[1], m[2] - V.campos[2]};
-        float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        float dir[3] = {d[0] * il, d[1] * il, d[2] * il};
-        float Y[16], dY[16][3];
+        const float4 rgbf = rec4[4 * e + 3], grgb4 = g2d[4 * e + 3];
+        const float gval[3] = {rgbf.y > 0.f ? grgb4.y : 0.f, rgbf.z > 0.f ? grgb4.z : 0.f,
+                               rgbf.w > 0.f ? grgb4.w : 0.f};
+        const float d[3] = {m[0] - V.campos[0], m[1] - V.campos[1], m[2] - V.campos[2]};
+        const float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const float dir[3] = {d[0] * il, d[1] * il, d[2] * il};
+        float Y[16], gY[16];
         sh_basis(dir[0], dir[1], dir[2], Y);
-        sh_basis_grad(dir[0], dir[1], dir[2], dY);
-        float val[3] = {0.5f, 0.5f, 0.5f};
+        {
+          float c[3 * K];
+          load_sh<T, K>(S, g, c);
 #pragma unroll
-        for (int j = 0; j < K; ++j)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) val[k] += Y[j] * c[3 * j + k];
-        float gval[3];
-        for (int k = 0; k < 3; ++k) gval[k] = val[k] > 0.f ? grgb[k] : 0.f;
-        float gdir[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-          const float gY = c[3 * j] * gval[0] + c[3 * j + 1] * gval[1] +
-                           c[3 * j + 2] * gval[2];
-          gdir[0] += gY * dY[j][0]; gdir[1] += gY * dY[j][1]; gdir[2] += gY * dY[j][2];
+          for (int j = 0; j < K; ++j) gY[j] = c[3 * j] * gval[0] + c[3 * j + 1] * gval[1] + c[3 * j + 2] * gval[2];
         }
-        float dd = dir[0] * gdir[0] + dir[1] * gdir[1] + dir[2] * gdir[2];
+        float gdir[3];
+        sh_basis_vjp<K>(dir[0], dir[1], dir[2], gY, gdir);
+        const float dd = dir[0] * gdir[0] + dir[1] * gdir[1] + dir[2] * gdir[2];
         for (int k = 0; k < 3; ++k) gm[k] += (gdir[k] - dir[k] * dd) * il;
         // dL/dc_jk = Y_j gval_k
         if (stage_sh) {
@@ -538,14 +535,21 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
           }
         } else if (Dg.dsh) {
           float* dst = Dg.dsh + 3 * K * g;
-          {
 #pragma unroll
-            for (int j = 0; j < K; ++j)
+          for (int j = 0; j < K; ++j)
 #pragma unroll
-              for (int k = 0; k < 3; ++k) put(dst, 3 * j + k, Y[j] * gval[k]);
-          }
+            for (int k = 0; k < 3; ++k) put(dst, 3 * j + k, Y[j] * gval[k]);
         }
       }
+      Geo geo;
+      geo_forward(V, m, s, q, lp, geo);
+      const Geo& gg = geo;
+      const float4 ga = g2d[4 * e], gb4 = g2d[4 * e + 1], gc4 = g2d[4 * e + 2], gd4 = g2d[4 * e + 3];
+      const float gu = ga.x, gv = ga.y, gca = ga.z, gcb = ga.w;
+      const float gcc = gb4.x, gz = gb4.w;
+      go = gb4.y;
+      const float gp0 = gc4.x, gp1 = gc4.y, gn[3] = {gc4.z, gc4.w, gd4.x};
+
       // ---- p = (z/t) q -----------------------------------------------------------
       const float it = 1.f / gg.tc;
       const float zt = gg.z * it;
