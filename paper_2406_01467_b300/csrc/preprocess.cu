@@ -455,7 +455,7 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
 // ---------------------------------------------------------------------------
 // FILT: the scene carries Mip-Splatting 3D filter variances.
 template <typename T, int D, bool FILT>
-__global__ void __launch_bounds__(kPreThreads)
+__global__ void __launch_bounds__(kPreThreads, 5)
 k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, GradPtrs gp) {
   constexpr int K = (D + 1) * (D + 1);
   const uint32_t* key = at<uint32_t>(ws, L.key);
