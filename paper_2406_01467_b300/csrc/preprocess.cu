@@ -270,7 +270,7 @@ __device__ inline void load_sh(const SceneDev& S, int64_t g, float* c) {
 // GEO: forward-only geometry (alpha, depth, normal); SH coefficients are not
 // read and the colour is left 0.  One launch covers every SH degree.
 template <typename T, int D, bool GEO>
-__global__ void __launch_bounds__(kPreThreads)
+__global__ void __launch_bounds__(kPreThreads, 5)
 k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
   constexpr int K = (D + 1) * (D + 1);
   Header* hdr = at<Header>(ws, L.hdr);
