@@ -439,9 +439,10 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
 // last items handed out are short and the tail is small.  The result does not depend on which warp takes
 // which item (each pixel is computed by exactly one warp).
 constexpr int kRenderThreads = 256;
+constexpr int kRenderBlocksPerSm = 3;
 
 template <bool LOSS, bool GEO>
-__global__ void __launch_bounds__(kRenderThreads)
+__global__ void __launch_bounds__(kRenderThreads, kRenderBlocksPerSm)
 k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_maps maps, int subs,
              int n_items) {
   __shared__ float4 s_rec[kRenderThreads / 32][2][4][32];
@@ -463,7 +464,7 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
 }
 
 template <bool LOSS>
-__global__ void __launch_bounds__(kRenderThreads)
+__global__ void __launch_bounds__(kRenderThreads, kRenderBlocksPerSm)
 k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_map_grads g, int subs,
              int n_items) {
   __shared__ float4 s_rec[kRenderThreads / 32][4][32];
@@ -495,7 +496,10 @@ static int persistent_grid(K kernel, int n_items) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kRenderThreads, 0);
   const int need = (n_items + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
-  int g = sms * (per_sm < 1 ? 1 : per_sm);
+  // three resident blocks (24 warps) per SM measured fastest for both kernels:
+  // a fourth adds issue contention and takes L1 capacity from the record reads
+  const int blocks = per_sm < 1 ? 1 : (per_sm < kRenderBlocksPerSm ? per_sm : kRenderBlocksPerSm);
+  int g = sms * blocks;
   return g < need ? g : (need < 1 ? 1 : need);
 }
 
