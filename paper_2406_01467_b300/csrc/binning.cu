@@ -379,7 +379,7 @@ k_digit_hist(const uint32_t* __restrict__ kin, const unsigned long long* count_p
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 3)
 k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
            uint32_t* __restrict__ vout, const unsigned long long* count_ptr, int64_t cap, int pass,
            const uint32_t* __restrict__ ghist, unsigned long long* __restrict__ look, int* ticket, Header* hdr) {
