@@ -361,15 +361,20 @@ k_digit_hist(const uint32_t* __restrict__ kin, const unsigned long long* count_p
   for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kSortThreads) (&s_h[0][0])[i] = 0;
   __syncthreads();
   const int64_t n = clamp_count(count_ptr, cap);
-  const unsigned lt = lanemask_lt();
   const int64_t step = (int64_t)gridDim.x * kSortThreads;
   for (int64_t i0 = (int64_t)blockIdx.x * kSortThreads; i0 < n; i0 += step) {   // warp-uniform loop
     const int64_t i = i0 + threadIdx.x;
     const uint32_t k = i < n ? __ldg(kin + i) : 0u;
+    const unsigned inb = __ballot_sync(FULL, i < n);
     for (int p = 0; p < passes; ++p) {
-      const int d = i < n ? (int)((k >> (kRadixBits * p)) & (kRadix - 1)) : kRadix;
-      const unsigned peers = __match_any_sync(FULL, d);
-      if (d < kRadix && (peers & lt) == 0) atomicAdd(&s_h[p][d], __popc(peers));
+      const int d = (int)((k >> (kRadixBits * p)) & (kRadix - 1));
+      // a digit shared by the whole warp (the high digits mostly are) costs one
+      // atomic; otherwise each lane adds its own (mostly distinct low digits)
+      if (__all_sync(FULL, d == __shfl_sync(FULL, d, 0) || i >= n)) {
+        if ((threadIdx.x & 31) == __ffs(inb) - 1) atomicAdd(&s_h[p][d], __popc(inb));
+      } else if (i < n) {
+        atomicAdd(&s_h[p][d], 1u);
+      }
     }
   }
   __syncthreads();
