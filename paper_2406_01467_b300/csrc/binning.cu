@@ -416,7 +416,8 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   for (int r = 0; r < kSortItems; ++r) {
     const bool ok = WarpItems::index(base, r) < n;
     const int d = ok ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
-    const unsigned peers = __match_any_sync(FULL, d);
+    // a digit shared by the whole warp needs no matching
+    const unsigned peers = __all_sync(FULL, d == __shfl_sync(FULL, d, 0)) ? FULL : __match_any_sync(FULL, d);
     const uint32_t old = d < kRadix ? s_wcnt[d][w] : 0u;
     rank[r] = old + __popc(peers & lt);
     __syncwarp();
