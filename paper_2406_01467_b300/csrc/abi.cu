@@ -182,6 +182,10 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   L.px_med = take(bwd_state ? 4 * (size_t)NPIX : 0);
   L.grad2d = take(bwd_state ? 64 * (size_t)E : 0);
   L.px_loss = take(p.losses ? 4 * (size_t)kLossPlanes * NPIX : 0);
+  // chunk k of tile t's list, 8x4 block b: word b * cmask_words + (start_t >> 5) + t + k;
+  // distinct for all (t, k) because floor(a/32) + floor(l/32) <= floor((a+l)/32)
+  L.cmask_words = (L.Pcap >> 5) + T + 2;
+  L.cmask = take(bwd_state ? 4 * (size_t)(p.tile_w * p.tile_h / 32) * (size_t)L.cmask_words : 0);
   L.total = off;
   return GS_OK;
 }

@@ -80,6 +80,13 @@ __device__ inline float quad(float a, float b, float c, float dx, float dy) {
   return 0.5f * (a * dx * dx + c * dy * dy) + b * dx * dy;
 }
 
+// The same with a fixed rounding sequence: the forward and the backward both
+// evaluate alpha through it, so they take identical alpha >= alpha_min decisions.
+__device__ inline float splat_sigma(float a, float b, float c, float dx, float dy) {
+  return __fmaf_rn(b, __fmul_rn(dx, dy),
+                   __fmul_rn(0.5f, __fmaf_rn(a, __fmul_rn(dx, dx), __fmul_rn(c, __fmul_rn(dy, dy)))));
+}
+
 // Minimum of sigma over the rectangle [X0, X1] x [Y0, Y1] (pixel-centre
 // coordinates): zero if the centre is inside, else the least of the four
 // edges' minima (each a 1D convex quadratic, clamped to the edge).
@@ -165,6 +172,8 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   const int lane = threadIdx.x & 31;
   const SubRect R = sub_rect(c.x0, c.y0, fd->tile_w / kSubW, sub);
 
+  // per-chunk masks of blended records of this 8x4 block (word k: chunk k of the list)
+  uint32_t* cmask = at<uint32_t>(ws, L.cmask) + (int64_t)sub * L.cmask_words + (range.x >> 5) + tile;
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, depth = 0.f;
   float Ws = 0.f, S1 = 0.f, S2 = 0.f, d0 = 0.f;   // Eq. 23 moments (LOSS only)
   int last = -1, med = -1;
@@ -186,6 +195,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
     float4 (*my)[32] = buf[cur];
     const bool rel = c0 + lane < range.y && reaches(my[0][lane], my[1][lane], R);
     unsigned m = __ballot_sync(kFull, rel);
+    uint32_t cm = 0;        // records of the chunk this lane blends
     while (m) {
       const int j = __ffs(m) - 1;
       m &= m - 1;
@@ -193,11 +203,12 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       ++evals;
       const float4 a = my[0][j], b = my[1][j];
       const float dx = a.x - fpx, dy = a.y - fpy;
-      const float sig = quad(a.z, a.w, b.x, dx, dy);
-      const float al = fminf(amax, b.y * __expf(-sig));
+      const float sig = splat_sigma(a.z, a.w, b.x, dx, dy);
+      const float al = fminf(amax, __fmul_rn(b.y, __expf(-sig)));
       if (al < amin) continue;
       const float Tn = T * (1.f - al);
       if (Tn < tmin) { done = true; continue; }
+      cm |= 1u << j;
       const float w = al * T;
       const float4 e2 = my[2][j], e3 = my[3][j];
       if (!GEO) { C0 += w * e3.y; C1 += w * e3.z; C2 += w * e3.w; }
@@ -216,6 +227,10 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       }
       last = c0 + j;
       T = Tn;
+    }
+    if (!GEO) {             // the backward replays only records some lane blended
+      const uint32_t wm = __reduce_or_sync(kFull, cm);
+      if (lane == 0) cmask[(c0 - range.x) >> 5] = wm;
     }
     __syncwarp();           // buf[cur] is refilled two chunks later
     cur ^= 1;
@@ -345,28 +360,28 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
   const float2 U01 = make_float2(dC[0], dC[1]), U23 = make_float2(dC[2], dN[0]), U45 = make_float2(dN[1], dN[2]);
   const float2 dN01 = make_float2(dN[0], dN[1]), dN2C0 = make_float2(dN[2], dC[0]), dC12 = make_float2(dC[1], dC[2]);
   const float2 nfp = make_float2(-fpx, -fpy);
-  for (int c1 = wmax + 1; c1 > range.x; c1 -= 32) {
-    const int i = c1 - 1 - lane;          // lane 0 holds the farthest record of the chunk
-    bool rel = false;
-    if (i >= range.x) {
-      const uint32_t e = pval[i];
+  // the forward's per-chunk masks name the records some lane of this block
+  // blended; the others have zero gradient here and are not replayed
+  const uint32_t* cmask = at<uint32_t>(ws, L.cmask) + (int64_t)sub * L.cmask_words + (range.x >> 5) + tile;
+  for (int k = wmax >= range.x ? (wmax - range.x) >> 5 : -1; k >= 0; --k) {
+    const uint32_t wm = cmask[k];
+    if (wm == 0) continue;
+    const int c0 = range.x + 32 * k;
+    if ((wm >> lane) & 1u) {
+      const uint32_t e = pval[c0 + lane];
       const float4* r = rec + 4 * (int64_t)e;
-      const float4 f0 = __ldg(r), f1 = __ldg(r + 1);
-      rel = reaches(f0, f1, R);
-      if (rel) {
-        my[0][lane] = f0;
-        my[1][lane] = f1;
-        my[2][lane] = __ldg(r + 2);
-        my[3][lane] = __ldg(r + 3);
-        my_e[lane] = e;
-      }
+      my[0][lane] = __ldg(r);
+      my[1][lane] = __ldg(r + 1);
+      my[2][lane] = __ldg(r + 2);
+      my[3][lane] = __ldg(r + 3);
+      my_e[lane] = e;
     }
-    unsigned m = __ballot_sync(kFull, rel);
+    unsigned m = wm;
     __syncwarp();
     while (m) {
-      const int j = __ffs(m) - 1;
-      m &= m - 1;
-      const int idx = c1 - 1 - j;
+      const int j = 31 - __clz(m);     // back to front
+      m &= ~(1u << j);
+      const int idx = c0 + j;
       // Branch-free: every lane evaluates the splat; lanes that do not blend it
       // (behind their last contributor, or alpha below alpha_min) take alpha = 0,
       // which leaves T and the running sums unchanged and zeroes every gradient.
@@ -378,9 +393,9 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float2 d = __fadd2_rn(make_float2(a.x, a.y), nfp);     // (dx, dy)
       const float dx = d.x, dy = d.y;
       const float2 d2 = __fmul2_rn(d, d);                           // (dx^2, dy^2)
-      const float sig = 0.5f * (a.z * d2.x + b.x * d2.y) + a.w * dx * dy;
+      const float sig = splat_sigma(a.z, a.w, b.x, dx, dy);
       const float G = __expf(-sig);
-      const float raw = b.y * G;
+      const float raw = __fmul_rn(b.y, G);
       const float al0 = fminf(amax, raw);
       const bool contrib = live && al0 >= amin;
       const float al = contrib ? al0 : 0.f;

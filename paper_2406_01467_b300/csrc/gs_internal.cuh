@@ -132,6 +132,8 @@ struct Layout {
   size_t px_T, px_last, px_med;
   size_t grad2d;            // [E][16] float
   size_t px_loss;           // [kLossPlanes][NPIX] float when losses, else 0 bytes
+  size_t cmask;             // [subs][cmask_words] uint: records each 8x4 block blended, per chunk
+  int64_t cmask_words;
   size_t total;
 };
 
