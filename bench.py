@@ -278,6 +278,7 @@ def run_ours(args, rank, world, device):
     pbytes = 4 * (3 + 3 + 4 + 1 + 3 * K)
     nvis, P = int(stats.n_visible), int(stats.n_pairs)
     ev_f, ev_b = int(stats.n_evals_fwd), int(stats.n_evals_bwd)
+    nbl = int(stats.n_blended)   # (pixel, splat) pairs blended: the compositing's algorithmic unit
     hbm = peaks["hbm_gbs"]
     alu_peak = N_SM * FP32_LANES * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # T lane-ops/s
     OPS_FWD, OPS_BWD = 20, 55
@@ -289,8 +290,10 @@ def run_ours(args, rank, world, device):
         "preprocess": ("hbm", N * gbytes + nvis * shbytes + nvis * 64 + N * 16),
         # bytes: per pair one read and one write per sort pass lower bound (24 B), depth keys
         "bin": ("hbm", P * 24 + nvis * 16 + N * 8),
-        "render_fwd": ("alu", ev_f * OPS_FWD),
-        "composite_bwd": ("alu", ev_b * OPS_BWD),
+        # ops: per blended (pixel, splat) pair (Eq. 3 sums over these); the
+        # evaluations the kernels spend on splats that end up not blended are overhead
+        "render_fwd": ("alu", nbl * OPS_FWD),
+        "composite_bwd": ("alu", nbl * OPS_BWD),
         # bytes: key of every entry, parameters + 2D gradients of visible entries read,
         # all parameter gradients written
         "preprocess_bwd": ("hbm", N * 4 + nvis * (pbytes + 64) + N * pbytes),
@@ -322,7 +325,7 @@ def run_ours(args, rank, world, device):
                    "image": f"{cam.width}x{cam.height}", "tile": f"{params.tile_w}x{params.tile_h}",
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
         "roofline": r, "stages": roof,
-        "counts": {"visible": nvis, "pairs": P, "evals_fwd": ev_f, "evals_bwd": ev_b},
+        "counts": {"visible": nvis, "pairs": P, "blended": nbl, "evals_fwd": ev_f, "evals_bwd": ev_b},
         "clocks": clocks, "e2e": e2e,
         "gpu_launches": launches_per_step(frame_tiles(cam, params)) * args.steps,
     }

@@ -181,6 +181,7 @@ typedef struct {
   int64_t n_nonfinite;  /* entries culled for non-finite inputs */
   int64_t n_evals_fwd;  /* (pixel, splat) evaluations of the last gs_render_fwd */
   int64_t n_evals_bwd;  /* (pixel, splat) evaluations of the last gs_composite_bwd */
+  int64_t n_blended;    /* (pixel, splat) pairs blended (Eq. 3) by the last gs_render_fwd */
   int32_t status;       /* sticky gs_status of the device work */
 } gs_stats;
 

@@ -72,7 +72,7 @@ APPEARANCE_STATE_FLOATS = 32
 class GsStats(Structure):
     _fields_ = [("n_entries", c_int64), ("n_visible", c_int64), ("n_pairs", c_int64),
                 ("n_nonfinite", c_int64), ("n_evals_fwd", c_int64), ("n_evals_bwd", c_int64),
-                ("status", c_int32)]
+                ("n_blended", c_int64), ("status", c_int32)]
 
 
 EXPORTS = ("gs_workspace_size", "gs_preprocess", "gs_bin", "gs_render_fwd", "gs_render_bwd",

@@ -401,6 +401,7 @@ gs_status gs_check(const gs_frame* frame, gs_stats* out, void* stream) {
     out->n_nonfinite = (int64_t)h.n_nonfinite;
     out->n_evals_fwd = (int64_t)h.n_evals_fwd;
     out->n_evals_bwd = (int64_t)h.n_evals_bwd;
+    out->n_blended = (int64_t)h.n_blend;
     out->status = h.status;
   }
   if (h.status == GS_ERR_CAPACITY)

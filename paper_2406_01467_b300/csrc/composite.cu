@@ -162,7 +162,8 @@ __device__ inline void stage_record(float4 (*chunk)[32], int lane, const float4*
 // pixels are done (after the copies in flight have landed).
 template <bool LOSS, bool GEO>
 __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restrict__ ws, const Layout& L,
-                                const gs_maps& maps, int tile, int sub, float4 (*buf)[4][32], uint32_t& evals) {
+                                const gs_maps& maps, int tile, int sub, float4 (*buf)[4][32], uint32_t& evals,
+                                uint32_t& blended) {
   const TileCtx c = tile_ctx(fd, tile, sub);
   const int2 range = at<int2>(ws, L.ranges)[tile];
   const uint32_t* pval = at<uint32_t>(ws, L.pval_final);
@@ -177,6 +178,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, depth = 0.f;
   float Ws = 0.f, S1 = 0.f, S2 = 0.f, d0 = 0.f;   // Eq. 23 moments (LOSS only)
   int last = -1, med = -1;
+  uint32_t nblend = 0;
   bool done = !c.inside;
   int cur = 0;
   uint32_t e_next = 0;   // entry of this lane's record in the chunk after the one in flight
@@ -228,6 +230,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       last = c0 + j;
       T = Tn;
     }
+    nblend += __popc(cm);
     if (!GEO) {             // the backward replays only records some lane blended
       const uint32_t wm = __reduce_or_sync(kFull, cm);
       if (lane == 0) cmask[(c0 - range.x) >> 5] = wm;
@@ -237,6 +240,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   }
   cp_async_wait<0>();       // no copy may land in the buffers after the item
   __syncwarp();
+  blended += nblend;
   if (!c.inside) return;
   if (med < 0 && last >= 0) {   // median never reached: depth of the last contributor
     med = last;
@@ -466,16 +470,17 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
   float4 (*buf)[4][32] = s_rec[threadIdx.x >> 5];
   const int* order = at<int>(ws, L.tile_order);
   const int lane = threadIdx.x & 31;
-  uint32_t evals = 0;
+  uint32_t evals = 0, blended = 0;
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(&hdr->work_fwd, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= n_items) break;
-    fwd_item<LOSS, GEO>(fd, ws, L, maps, order[item / subs], item % subs, buf, evals);
+    fwd_item<LOSS, GEO>(fd, ws, L, maps, order[item / subs], item % subs, buf, evals, blended);
     __syncwarp();
   }
   count_evals(evals, &hdr->n_evals_fwd);
+  count_evals(blended, &hdr->n_blend);
 }
 
 template <bool LOSS>
@@ -523,6 +528,7 @@ cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& hf, con
   const FrameDev* fd = at<FrameDev>(ws, L.frame);
   Header* hdr = at<Header>(ws, L.hdr);
   cudaError_t err = cudaMemsetAsync(&hdr->n_evals_fwd, 0, 8, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(&hdr->n_blend, 0, 8, s);
   if (err == cudaSuccess) err = cudaMemsetAsync(&hdr->work_fwd, 0, 4, s);
   if (err != cudaSuccess) return err;
   if (L.T == 0) return cudaSuccess;

@@ -112,7 +112,8 @@ struct Header {
   int32_t status;
   int32_t work_fwd, work_bwd;   // work-queue counters of the persistent compositing kernels
   uint32_t filter_max;          // bits of the largest 3D-filter variance of seen Gaussians
-  int32_t pad_[50];
+  unsigned long long n_blend;   // (pixel, splat) pairs blended by the last forward
+  int32_t pad_[48];
 };
 
 // Byte offsets of every buffer inside the caller's workspace.
