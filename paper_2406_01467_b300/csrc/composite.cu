@@ -441,12 +441,12 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float2 guv = __ffma2_rn(make_float2(gs, gs), mm, __fmul2_rn(make_float2(sd, sd),
                                                                           make_float2(e2.x, e2.y)));
       gr[0] = guv;
-      if (__any_sync(kFull, contrib)) {
-        const float s = warp_reduce_scatter16(gr, my_red);
-        const int slot = lane >> 1;
-        if ((lane & 1) == 0 && slot != R_CUT && s != 0.f)
-          atomicAdd(grad + (int64_t)my_e[j] * kRecFloats + slot, s);
-      }
+      // some lane blends every replayed record (the forward's mask), so every
+      // visit reduces
+      const float s = warp_reduce_scatter16(gr, my_red);
+      const int slot = lane >> 1;
+      if ((lane & 1) == 0 && slot != R_CUT && s != 0.f)
+        atomicAdd(grad + (int64_t)my_e[j] * kRecFloats + slot, s);
     }
     __syncwarp();
   }
