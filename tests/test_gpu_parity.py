@@ -113,9 +113,12 @@ def _upstream(cam, seed, ambiguous_mask=None):
     return up
 
 
-def test_backward_matches_oracle_tiny():
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 8), (32, 8)])
+def test_backward_matches_oracle_tiny(tile):
+    # the backward replays the records each 8x4 block blended in the forward:
+    # every tile size (2, 4 or 8 blocks per tile) must give the oracle's gradients
     sc, cam = scenes.tiny_scene(), scenes.tiny_camera()
-    p = RenderParams()
+    p = RenderParams(tile_w=tile[0], tile_h=tile[1])
     op = oracle_params(p)
     ref_f = oracle.render(sc, cam, op)
     amb = ref_f["margin"] < AMBIG_MARGIN
