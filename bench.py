@@ -168,6 +168,71 @@ def launches_per_step(n_tiles, n_dtypes=1):
 # --------------------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------------------
+def e2e_pipelined(st, cam, params, capacity, host, n_steps, device):
+    """ms per step of the end-to-end loop (parameters uploaded from pinned host
+    memory, maps and gradients downloaded to pinned host memory, every step) with
+    the copies of neighbouring steps overlapping the compute: two slots of device
+    parameters, frame and gradients; an upload stream, a compute stream and a
+    download stream ordered by events."""
+    import torch
+    from paper_2406_01467_b300 import Frame, SceneTensors, scenes
+    keys = ("means", "scales", "quats", "opacities", "sh")
+    up = [torch.from_numpy(u[0]).to(device) for u in scenes.upstream_grads(11, cam.height, cam.width)]
+    slots = []
+    for _ in range(2):
+        sts = SceneTensors(*(getattr(st, k).clone() for k in keys), st.sh_degree)
+        fr = Frame([sts], [(cam, 0)], params, pair_capacity=capacity)
+        g = fr.alloc_grads()
+        outs = {k: torch.empty(getattr(fr, k).shape, dtype=torch.float32).pin_memory()
+                for k in ("color", "alpha", "depth", "normal")}
+        gouts = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in g[0].items()}
+        ev = {n: torch.cuda.Event() for n in ("h2d", "comp", "d2h")}
+        slots.append((sts, fr, g, outs, gouts, ev))
+    s_up, s_comp, s_down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+
+    def issue(i):
+        sts, fr, g, outs, gouts, ev = slots[i % 2]
+        with torch.cuda.stream(s_up):      # the slot's previous compute has read its parameters
+            s_up.wait_event(ev["comp"])
+            for k in keys:
+                getattr(sts, k).copy_(host[k], non_blocking=True)
+            ev["h2d"].record(s_up)
+        with torch.cuda.stream(s_comp):    # ... and its previous results have been downloaded
+            s_comp.wait_event(ev["h2d"])
+            s_comp.wait_event(ev["d2h"])
+            fr.preprocess()
+            fr.bin()
+            fr.render()
+            fr.backward(*up, grads=g, split=True)
+            ev["comp"].record(s_comp)
+        with torch.cuda.stream(s_down):
+            s_down.wait_event(ev["comp"])
+            for k, v in outs.items():
+                v.copy_(getattr(fr, k), non_blocking=True)
+            for k, v in gouts.items():
+                v.copy_(g[0][k], non_blocking=True)
+            ev["d2h"].record(s_down)
+
+    for i in range(4):
+        issue(i)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream()
+    a.record(cur)
+    for s_ in (s_up, s_comp, s_down):
+        s_.wait_stream(cur)
+    for i in range(n_steps):
+        issue(i)
+    for s_ in (s_up, s_comp, s_down):
+        cur.wait_stream(s_)
+    b.record(cur)
+    torch.cuda.synchronize()
+    for sl in slots:
+        if sl[1].stats().status != 0:
+            raise RuntimeError("end-to-end frame status %d" % sl[1].last_status)
+    return a.elapsed_time(b) / n_steps
+
+
 def run_ours(args, rank, world, device):
     import torch
     from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, scenes
@@ -266,9 +331,13 @@ def run_ours(args, rank, world, device):
             e2e_step()
         b.record()
         torch.cuda.synchronize()
-        e2e_ms = max_over_ranks(a.elapsed_time(b) / n_e2e, device)
+        e2e_serial = max_over_ranks(a.elapsed_time(b) / n_e2e, device)
+        e2e_ms = e2e_pipelined(st, cam, params, frame.pair_capacity, host, n_e2e, device)
+        e2e_ms = max_over_ranks(e2e_ms, device)
         e2e = {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
+               "d2h_bytes_per_step": int(d2h), "steps": n_e2e, "serial_ms": round(e2e_serial, 4),
+               "how": "two slots on three streams: step k+1's parameter upload and step k-1's "
+                      "map/gradient download overlap step k's compute"}
 
     # ---- roofline ---------------------------------------------------------------------------
     peaks, src = load_peaks()
