@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kSortThreads, 3)
 k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
            uint32_t* __restrict__ vout, const unsigned long long* count_ptr, int64_t cap, int pass,
            const uint32_t* __restrict__ ghist, unsigned long long* __restrict__ look, int* ticket, Header* hdr) {
-  __shared__ uint32_t s_wcnt[kRadix][8];
+  __shared__ uint32_t s_wcnt[8][kRadix];   // [warp][digit]: per-lane digit accesses spread over the banks
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
   __shared__ uint32_t s_dstart[kRadix];
@@ -418,16 +418,16 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
     const int d = ok ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
     // a digit shared by the whole warp needs no matching
     const unsigned peers = __all_sync(FULL, d == __shfl_sync(FULL, d, 0)) ? FULL : __match_any_sync(FULL, d);
-    const uint32_t old = d < kRadix ? s_wcnt[d][w] : 0u;
+    const uint32_t old = d < kRadix ? s_wcnt[w][d] : 0u;
     rank[r] = old + __popc(peers & lt);
     __syncwarp();
-    if (d < kRadix && (peers & lt) == 0) s_wcnt[d][w] = old + __popc(peers);
+    if (d < kRadix && (peers & lt) == 0) s_wcnt[w][d] = old + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
   const int d = threadIdx.x;   // one thread per digit from here on
   uint32_t c[8], cnt = 0;
-  for (int i = 0; i < 8; ++i) { c[i] = s_wcnt[d][i]; cnt += c[i]; }
+  for (int i = 0; i < 8; ++i) { c[i] = s_wcnt[i][d]; cnt += c[i]; }
   unsigned long long* mine = look + (int64_t)blk * kRadix + d;
   st_relaxed(mine, (blk == 0 ? kFlagP : kFlagA) | cnt);   // successors may start looking
   // block-local exclusive scan over (digit, warp) in digit-major order, and the
@@ -436,7 +436,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   const uint32_t dbase = block_exclusive_scan(ghist[pass * kRadix + d], s_warp, nullptr);
   s_dstart[d] = start;
   uint32_t run = start;
-  for (int i = 0; i < 8; ++i) { s_wcnt[d][i] = run; run += c[i]; }
+  for (int i = 0; i < 8; ++i) { s_wcnt[i][d] = run; run += c[i]; }
   // decoupled look-back: keys of digit d in the blocks before this one
   uint32_t excl = 0;
   if (blk > 0) {
@@ -460,7 +460,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
     const int64_t i = WarpItems::index(base, r);
     if (i < n) {
       const int dd = (int)((k[r] >> shift) & (kRadix - 1));
-      const uint32_t pos = s_wcnt[dd][w] + rank[r];
+      const uint32_t pos = s_wcnt[w][dd] + rank[r];
       s_keys[pos] = k[r];
       s_vals[pos] = v[r];
     }
