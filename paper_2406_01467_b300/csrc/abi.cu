@@ -166,6 +166,7 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   L.touched = take(4 * (size_t)E);
   for (int i = 0; i < 2; ++i) { L.vkey[i] = take(4 * (size_t)E); L.vval[i] = take(4 * (size_t)E); }
   L.pair_off = take(4 * (size_t)E);
+  L.chunk_first = take(4 * (size_t)((L.Pcap + kEmitChunk - 1) / kEmitChunk + 1));
   const int nbmax = std::max(L.nb_E, L.nb_P);
   L.blk = take(4 * (size_t)nbmax);
   for (int i = 0; i < 2; ++i) { L.ptile[i] = take(4 * (size_t)L.Pcap); L.pval[i] = take(4 * (size_t)L.Pcap); }

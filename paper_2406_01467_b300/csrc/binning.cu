@@ -172,7 +172,7 @@ k_compact(const uint32_t* __restrict__ key, int64_t E, const uint32_t* __restric
 __global__ void __launch_bounds__(kSortThreads)
 k_pair_offsets(const uint32_t* __restrict__ sval, const unsigned long long* n_vis_ptr, int64_t E,
                const uint32_t* __restrict__ touched, const uint32_t* __restrict__ blk,
-               uint32_t* __restrict__ pair_off) {
+               uint32_t* __restrict__ pair_off, uint32_t* __restrict__ chunk_first, int64_t n_chunks) {
   __shared__ uint32_t s_wtot[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t n = clamp_count(n_vis_ptr, E);
@@ -203,7 +203,14 @@ k_pair_offsets(const uint32_t* __restrict__ sval, const unsigned long long* n_vi
       if (lane >= o) x += y;
     }
     const int64_t i = WarpItems::index(base, r);
-    if (i < n) pair_off[i] = off + x - cnt[r];
+    if (i < n) {
+      const uint32_t o = off + x - cnt[r];
+      pair_off[i] = o;
+      // the entry that holds the first pair of every emission chunk starting in it
+      const int64_t qe = ((int64_t)o + cnt[r] - 1) / kEmitChunk;
+      for (int64_t q = ((int64_t)o + kEmitChunk - 1) / kEmitChunk; cnt[r] && q <= qe && q < n_chunks; ++q)
+        chunk_first[q] = (uint32_t)i;
+    }
     off += __shfl_sync(FULL, x, 31);
   }
 }
@@ -219,18 +226,19 @@ __device__ inline int64_t last_le(const uint32_t* off, int64_t n, uint32_t p) {
 }
 
 // Emission of (tile, entry) pairs in depth order, load-balanced over the whole
-// grid: block slice c writes pairs [c * kEmitChunk, (c + 1) * kEmitChunk).  Two
-// binary searches over pair_off give the slice's entry range (at most one
-// entry per pair, so it fits in shared memory); each thread then finds the
-// entry of each of its pairs by a short search there.  Stores are contiguous
+// grid: block slice c writes pairs [c * kEmitChunk, (c + 1) * kEmitChunk).  The
+// pair-offset kernel records the entry holding each slice's first pair, which
+// gives the slice's entry range (at most one entry per pair, so it fits in
+// shared memory; only a slice cut short by the capacity searches pair_off);
+// each thread then finds the entry of each of its pairs by a short search there.  Stores are contiguous
 // and a splat covering hundreds of tiles is shared by many threads.
-constexpr int kEmitChunk = 2048;
 
 __global__ void __launch_bounds__(kSortThreads)
 k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
        const unsigned long long* n_vis_ptr, const unsigned long long* n_pairs_ptr, int64_t E,
        const short4* __restrict__ rect, const uint32_t* __restrict__ pair_off, int64_t cap,
-       uint32_t* __restrict__ ptile, uint32_t* __restrict__ pval) {
+       uint32_t* __restrict__ ptile, uint32_t* __restrict__ pval, const uint32_t* __restrict__ chunk_first,
+       int64_t n_chunks) {
   __shared__ uint32_t s_off[kEmitChunk + 1], s_ent[kEmitChunk + 1];
   __shared__ short4 s_rc[kEmitChunk + 1];
   __shared__ int64_t s_k[2];
@@ -242,7 +250,16 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
   for (int64_t p0 = (int64_t)blockIdx.x * kEmitChunk; p0 < P; p0 += (int64_t)gridDim.x * kEmitChunk) {
     const int64_t p1 = min(P, p0 + kEmitChunk);
     __syncthreads();
-    if (threadIdx.x < 2) s_k[threadIdx.x] = last_le(pair_off, n, (uint32_t)(threadIdx.x ? p1 - 1 : p0));
+    if (threadIdx.x == 0) {   // entries holding pairs p0 and p1 - 1 (every entry holds >= 1 pair)
+      const int64_t q = p0 / kEmitChunk;
+      s_k[0] = chunk_first[q];
+      if (p1 < P && q + 1 < n_chunks) {   // pair p1 exists, so its entry is in the table
+        const uint32_t e1 = chunk_first[q + 1];
+        s_k[1] = __ldg(pair_off + e1) == (uint32_t)p1 ? (int64_t)e1 - 1 : (int64_t)e1;
+      } else {
+        s_k[1] = last_le(pair_off, n, (uint32_t)(p1 - 1));
+      }
+    }
     __syncthreads();
     const int64_t k0 = s_k[0];
     const int m = (int)(s_k[1] - k0 + 1);
@@ -529,10 +546,13 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   k_scan_partials<<<1, 1024, 0, s>>>(blk, L.nb_E, &hdr->n_pairs, L.Pcap, hdr);
   // 4. emission
   uint32_t* pair_off = at<uint32_t>(ws, L.pair_off);
-  k_pair_offsets<<<L.nb_E, kSortThreads, 0, s>>>(vv0, &hdr->n_vis, L.E, touched, blk, pair_off);
+  uint32_t* chunk_first = at<uint32_t>(ws, L.chunk_first);
+  const int64_t n_chunks = (L.Pcap + kEmitChunk - 1) / kEmitChunk + 1;
+  k_pair_offsets<<<L.nb_E, kSortThreads, 0, s>>>(vv0, &hdr->n_vis, L.E, touched, blk, pair_off, chunk_first,
+                                                  n_chunks);
   const int eg = (int)std::min<int64_t>((L.Pcap + kEmitChunk - 1) / kEmitChunk, 148 * 8);
   k_emit<<<eg, kSortThreads, 0, s>>>(fd, vv0, &hdr->n_vis, &hdr->n_pairs, L.E, at<short4>(ws, L.rect),
-                                     pair_off, L.Pcap, pt0, pv0);
+                                     pair_off, L.Pcap, pt0, pv0, chunk_first, n_chunks);
   // 5. tile sort
   const int bits = tile_sort_bits(L.T);
   err = radix_sort(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, aux, L.sortaux_bytes, hdr, s);

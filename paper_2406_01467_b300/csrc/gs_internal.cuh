@@ -16,6 +16,7 @@ constexpr int kSortThreads = 256;         // radix sort / scan block size
 constexpr int kSortItems = 16;            // items per thread
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 items per block
 constexpr int kRadixBits = 8;
+constexpr int kEmitChunk = 2048;          // pairs per emission slice
 constexpr int kRadix = 1 << kRadixBits;
 
 // Record slots (one 64-byte record per (view, Gaussian) entry).
@@ -123,6 +124,7 @@ struct Layout {
   size_t hdr, frame, rec, rect, key, touched;
   size_t vkey[2], vval[2];  // depth sort ping-pong
   size_t pair_off;          // exclusive scan of tiles_touched in depth order
+  size_t chunk_first;       // [Pcap / kEmitChunk + 1] entry holding each emission chunk's first pair
   size_t blk;               // per-block partials of the scans
   size_t ptile[2], pval[2]; // pair sort ping-pong
   size_t ptile_final, pval_final;  // where the sorted pairs end up
