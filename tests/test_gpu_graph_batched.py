@@ -86,3 +86,34 @@ def test_bf16_storage_error_on_central_crop():
     print("bf16 compute error (same rounded inputs):", rep)
     print("bf16 storage error (fp32 inputs):", errs)
     assert all(np.isfinite(v) for v in errs.values())
+
+
+def test_bf16_filtered_losses_multiview_matches_fp32_on_rounded_inputs():
+    # every option at once: BF16 storage, 3D filter, loss maps, two views of two
+    # scenes; against the FP32 path fed the same BF16-rounded parameters
+    r = scenes.to_bf16_rounded
+    rng = np.random.default_rng(4)
+    scs = []
+    for seed in (5, 6):
+        s = scenes.object_scene(20_000, seed=seed)
+        s = scenes.Scene(r(s.means), r(s.scales), r(s.quats), r(s.opacities), r(s.sh), s.sh_degree)
+        s.filter_var = rng.uniform(0.0, 1e-5, s.n).astype(np.float32)
+        scs.append(s)
+    views = [(scenes.object_camera(257, 193, 330.0), 0), (scenes.object_camera(240, 176, 300.0), 1)]
+    p = RenderParams(losses=True)
+    outs = []
+    for dt in (torch.bfloat16, torch.float32):
+        fr = Frame([SceneTensors.from_scene(s, DEV, dt) for s in scs], views, p)
+        fr.forward()
+        ups = [torch.randn(k * fr.n_pixels, device=DEV, generator=torch.Generator(device=DEV).manual_seed(k))
+               for k in (3, 1, 1, 3, 1, 1)]
+        g = fr.backward(*ups[:4], ddist=ups[4], dnloss=ups[5])
+        torch.cuda.synchronize()
+        assert fr.stats().status == 0
+        outs.append(([t.clone() for v in range(2) for t in fr.view_maps(v) + fr.loss_maps(v)], g))
+    for a, b in zip(outs[0][0], outs[1][0]):
+        torch.testing.assert_close(a, b, rtol=1e-4, atol=1e-4)
+    for ga, gb in zip(outs[0][1], outs[1][1]):
+        for k in ga:
+            s_ = gb[k].abs().max().item()
+            assert (ga[k] - gb[k]).abs().max().item() <= 1e-3 * s_ + 1e-12, k
