@@ -300,6 +300,12 @@ def run_ours(args, rank, world, device):
         stages["preprocess_bwd"] += ev[4].elapsed_time(ev[5])
     stages = {k: v / args.steps for k, v in stages.items()}
     ms = max_over_ranks(ms_total / args.steps, device)
+    # the same step captured once as a CUDA graph and replayed (no host launch
+    # work, fewer inter-kernel gaps); reported beside the eager figure
+    from paper_2406_01467_b300 import autotune
+    graph = autotune.capture(step)
+    ms_graph = max_over_ranks(autotune.time_step(graph.replay, args.steps), device)
+    del graph
 
     # ---- end to end: host parameters in, host maps and gradients out --------------------
     e2e = None
@@ -393,6 +399,7 @@ def run_ours(args, rank, world, device):
         "config": {"workload": CONFIGS[args.config]["workload"], "gaussians": N,
                    "image": f"{cam.width}x{cam.height}", "tile": f"{params.tile_w}x{params.tile_h}",
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+        "ms_per_step_graph": round(ms_graph, 4),
         "roofline": r, "stages": roof,
         "counts": {"visible": nvis, "pairs": P, "blended": nbl, "evals_fwd": ev_f, "evals_bwd": ev_b},
         "clocks": clocks, "e2e": e2e,
