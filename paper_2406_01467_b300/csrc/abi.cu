@@ -173,14 +173,18 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   const int passes = (tile_sort_bits(T) + kRadixBits - 1) / kRadixBits;
   L.ptile_final = L.ptile[passes & 1];
   L.pval_final = L.pval[passes & 1];
-  L.sortaux_bytes = 8192 + (size_t)4 * nbmax * kRadix * 8;   // histograms + tickets, 4 passes of look-back
-  L.sortaux = take(L.sortaux_bytes);
+  // histograms + tickets, then 4 passes (depth) or the tile passes of look-back words
+  L.sortaux_bytes[0] = 8192 + (size_t)4 * L.nb_E * kRadix * 8;
+  L.sortaux_bytes[1] = 8192 + (size_t)4 * L.nb_P * kRadix * 8;
+  L.sortaux[0] = take(L.sortaux_bytes[0]);   // these three regions are contiguous:
+  L.sortaux[1] = take(L.sortaux_bytes[1]);   // binning clears them with one memset
   L.ranges = take(8 * (size_t)T);
   L.tile_order = take(4 * (size_t)T);
   const bool bwd_state = !p.geometry_only;   // per-pixel replay state and 2D gradients
   L.px_T = take(bwd_state ? 4 * (size_t)NPIX : 0);
   L.px_last = take(bwd_state ? 4 * (size_t)NPIX : 0);
   L.px_med = take(bwd_state ? 4 * (size_t)NPIX : 0);
+  L.bwdcnt = take(bwd_state ? 256 : 0);       // contiguous with grad2d: one memset clears both
   L.grad2d = take(bwd_state ? 64 * (size_t)E : 0);
   L.px_loss = take(p.losses ? 4 * (size_t)kLossPlanes * NPIX : 0);
   // chunk k of tile t's list, 8x4 block b: word b * cmask_words + (start_t >> 5) + t + k;
@@ -401,7 +405,12 @@ gs_status gs_check(const gs_frame* frame, gs_stats* out, void* stream) {
     out->n_pairs = (int64_t)h.n_pairs;
     out->n_nonfinite = (int64_t)h.n_nonfinite;
     out->n_evals_fwd = (int64_t)h.n_evals_fwd;
-    out->n_evals_bwd = (int64_t)h.n_evals_bwd;
+    BwdCounters bc = {0, 0, 0};
+    if (!fd.geometry_only) {
+      e = cudaMemcpy(&bc, at<BwdCounters>(frame->workspace, L.bwdcnt), sizeof(bc), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e, "reading the backward counters");
+    }
+    out->n_evals_bwd = (int64_t)bc.n_evals_bwd;
     out->n_blended = (int64_t)h.n_blend;
     out->status = h.status;
   }

@@ -502,8 +502,7 @@ static cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t
   uint32_t* ghist = static_cast<uint32_t*>(aux);                       // [kMaxPasses][256]
   int* tickets = reinterpret_cast<int*>(ghist + kMaxPasses * kRadix);   // [kMaxPasses]
   unsigned long long* look = reinterpret_cast<unsigned long long*>(static_cast<char*>(aux) + 8192);
-  cudaError_t e = cudaMemsetAsync(aux, 0, std::min(aux_bytes, (size_t)8192 + (size_t)passes * nb * kRadix * 8), s);
-  if (e != cudaSuccess) return e;
+  (void)aux_bytes;   // cleared by the binning's single memset
   k_digit_hist<<<std::min(nb, 148 * 8), kSortThreads, 0, s>>>(k0, count, cap, passes, ghist);
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
   for (int p = 0; p < passes; ++p) {
@@ -533,13 +532,16 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   uint32_t *pt0 = at<uint32_t>(ws, L.ptile[0]), *pt1 = at<uint32_t>(ws, L.ptile[1]);
   uint32_t *pv0 = at<uint32_t>(ws, L.pval[0]), *pv1 = at<uint32_t>(ws, L.pval[1]);
   (void)hf;
+  // 0. one memset clears both sorts' auxiliary words and the tile ranges (contiguous)
+  cudaError_t e0 = cudaMemsetAsync(at<char>(ws, L.sortaux[0]), 0, L.ranges + 8 * (size_t)L.T - L.sortaux[0], s);
+  if (e0 != cudaSuccess) return e0;
   // 1. compaction
   k_block_sums<0><<<L.nb_E, kSortThreads, 0, s>>>(key, nullptr, nullptr, L.E, blk);
   k_scan_partials<<<1, 1024, 0, s>>>(blk, L.nb_E, &hdr->n_vis, 0, hdr);
   k_compact<<<L.nb_E, kSortThreads, 0, s>>>(key, L.E, blk, vk0, vv0);
   // 2. depth sort: 31 bits (z > 0, so the sign bit is clear)
-  void* aux = at<void>(ws, L.sortaux);
-  cudaError_t err = radix_sort(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, aux, L.sortaux_bytes, hdr, s);
+  cudaError_t err = radix_sort(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, at<void>(ws, L.sortaux[0]),
+                               L.sortaux_bytes[0], hdr, s);
   if (err != cudaSuccess) return err;
   // 3. pair offsets
   k_block_sums<1><<<L.nb_E, kSortThreads, 0, s>>>(touched, vv0, &hdr->n_vis, L.E, blk);
@@ -555,11 +557,11 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
                                      pair_off, L.Pcap, pt0, pv0, chunk_first, n_chunks);
   // 5. tile sort
   const int bits = tile_sort_bits(L.T);
-  err = radix_sort(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, aux, L.sortaux_bytes, hdr, s);
+  err = radix_sort(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, at<void>(ws, L.sortaux[1]),
+                   L.sortaux_bytes[1], hdr, s);
   if (err != cudaSuccess) return err;
   uint32_t* ptile = at<uint32_t>(ws, L.ptile_final);
   // 6. ranges
-  cudaMemsetAsync(at<int2>(ws, L.ranges), 0, sizeof(int2) * (size_t)L.T, s);
   int g = (int)std::min<int64_t>((L.Pcap + 255) / 256, 148 * 32);
   k_ranges<<<g, 256, 0, s>>>(ptile, &hdr->n_pairs, L.Pcap, at<int2>(ws, L.ranges));
   // 7. compositing work order (by list length)

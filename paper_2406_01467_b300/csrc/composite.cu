@@ -491,6 +491,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
   __shared__ uint32_t s_ent[kRenderThreads / 32][32];
   __shared__ __align__(16) float s_red[kRenderThreads / 32][16 * kRedStride];
   Header* hdr = at<Header>(ws, L.hdr);
+  BwdCounters* bc = at<BwdCounters>(ws, L.bwdcnt);
   if (hdr->status == GS_ERR_CAPACITY) return;
   float4 (*my)[32] = s_rec[threadIdx.x >> 5];
   uint32_t* my_e = s_ent[threadIdx.x >> 5];
@@ -499,13 +500,13 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
   uint32_t evals = 0;
   for (;;) {
     int item = 0;
-    if (lane == 0) item = atomicAdd(&hdr->work_bwd, 1);
+    if (lane == 0) item = atomicAdd(&bc->work_bwd, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= n_items) break;
     bwd_item<LOSS>(fd, ws, L, g, order[item / subs], item % subs, my, my_e, s_red[threadIdx.x >> 5], evals);
     __syncwarp();
   }
-  count_evals(evals, &hdr->n_evals_bwd);
+  count_evals(evals, &bc->n_evals_bwd);
 }
 
 // A resident wave of blocks for a persistent kernel.
@@ -527,9 +528,7 @@ cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& hf, con
                               cudaStream_t s) {
   const FrameDev* fd = at<FrameDev>(ws, L.frame);
   Header* hdr = at<Header>(ws, L.hdr);
-  cudaError_t err = cudaMemsetAsync(&hdr->n_evals_fwd, 0, 8, s);
-  if (err == cudaSuccess) err = cudaMemsetAsync(&hdr->n_blend, 0, 8, s);
-  if (err == cudaSuccess) err = cudaMemsetAsync(&hdr->work_fwd, 0, 4, s);
+  cudaError_t err = cudaMemsetAsync(&hdr->n_evals_fwd, 0, 24, s);   // n_evals_fwd, n_blend, work_fwd
   if (err != cudaSuccess) return err;
   if (L.T == 0) return cudaSuccess;
   const int subs = hf.tile_w * hf.tile_h / 32;
@@ -550,10 +549,9 @@ cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& hf, con
                               cudaStream_t s) {
   const FrameDev* fd = at<FrameDev>(ws, L.frame);
   Header* hdr = at<Header>(ws, L.hdr);
-  cudaError_t err = cudaMemsetAsync(at<float>(ws, L.grad2d), 0,
-                                    sizeof(float) * kRecFloats * (size_t)L.E, s);
-  if (err == cudaSuccess) err = cudaMemsetAsync(&hdr->n_evals_bwd, 0, 8, s);
-  if (err == cudaSuccess) err = cudaMemsetAsync(&hdr->work_bwd, 0, 4, s);
+  // the backward counters and the 2D gradients are contiguous: one memset
+  cudaError_t err = cudaMemsetAsync(at<char>(ws, L.bwdcnt), 0,
+                                    L.grad2d + sizeof(float) * kRecFloats * (size_t)L.E - L.bwdcnt, s);
   if (err != cudaSuccess) return err;
   if (L.T == 0) return cudaSuccess;
   const int subs = hf.tile_w * hf.tile_h / 32;

@@ -108,13 +108,22 @@ struct Header {
   unsigned long long n_vis;
   unsigned long long n_pairs;
   unsigned long long n_nonfinite;
+  // reset together (one 24-byte memset) before every forward render
   unsigned long long n_evals_fwd;
-  unsigned long long n_evals_bwd;
-  int32_t status;
-  int32_t work_fwd, work_bwd;   // work-queue counters of the persistent compositing kernels
-  uint32_t filter_max;          // bits of the largest 3D-filter variance of seen Gaussians
   unsigned long long n_blend;   // (pixel, splat) pairs blended by the last forward
-  int32_t pad_[48];
+  int32_t work_fwd;             // work-queue counter of the persistent forward
+  int32_t pad0_;
+  int32_t status;
+  uint32_t filter_max;          // bits of the largest 3D-filter variance of seen Gaussians
+  int32_t pad_[50];
+};
+
+// Counters of the compositing backward; they sit right before the 2D-gradient
+// buffer so that one memset clears both.
+struct BwdCounters {
+  unsigned long long n_evals_bwd;
+  int32_t work_bwd;             // work-queue counter of the persistent backward
+  int32_t pad_;
 };
 
 // Byte offsets of every buffer inside the caller's workspace.
@@ -128,11 +137,12 @@ struct Layout {
   size_t blk;               // per-block partials of the scans
   size_t ptile[2], pval[2]; // pair sort ping-pong
   size_t ptile_final, pval_final;  // where the sorted pairs end up
-  size_t sortaux;           // radix sort: digit histograms, tickets, look-back words
-  size_t sortaux_bytes;
+  size_t sortaux[2];        // depth and tile radix sorts: digit histograms, tickets, look-back
+  size_t sortaux_bytes[2];  // words; both and the tile ranges are cleared by one memset
   size_t ranges;            // [T] int2
   size_t tile_order;        // [T] int: compositing work order (heaviest tiles first)
   size_t px_T, px_last, px_med;
+  size_t bwdcnt;            // BwdCounters (one 256-byte block right before grad2d)
   size_t grad2d;            // [E][16] float
   size_t px_loss;           // [kLossPlanes][NPIX] float when losses, else 0 bytes
   size_t cmask;             // [subs][cmask_words] uint: records each 8x4 block blended, per chunk
