@@ -276,32 +276,54 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   }
 }
 
-// Warp reduce-scatter of 16 values held as 8 pairs (v[k] = slots 2k, 2k+1)
-// through the warp's shared scratch red[16][kRedStride]: every lane stores its
-// 16 values (red[slot][lane]), then lane l adds slot l >> 1 over one half of
-// the warp with four 16-byte loads and lanes l, l^1 combine their halves.
-// Afterwards lane l holds the warp-wide sum of slot (l >> 1).  The row stride
-// of 36 floats keeps both the stores and the 16-byte loads free of bank
-// conflicts.
+// Warp reductions of gradient rows.  Every lane stores its values into the
+// warp's shared scratch as rows red[slot][lane] (row stride kRedStride = 36
+// floats: the row stores and the 16-byte row loads below are both free of bank
+// conflicts), then lanes add rows.
+//  - 16 rows (one record): lane l adds row l >> 1 over one half of the warp
+//    with four 16-byte loads; lanes l, l^1 combine their halves, after which
+//    lane l holds the warp-wide sum of slot l >> 1.
+//  - 32 rows (two records): lane l adds all of row l with eight 16-byte loads
+//    and holds the sum of slot l & 15 of record l >> 4; no shuffle.
 constexpr int kRedStride = 36;
 
-__device__ inline float warp_reduce_scatter16(const float2 (&v)[8], float* __restrict__ red) {
+__device__ inline void store_rows16(const float2 (&v)[8], float* __restrict__ red) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     red[(2 * k) * kRedStride + lane] = v[k].x;
     red[(2 * k + 1) * kRedStride + lane] = v[k].y;
   }
-  __syncwarp();
+}
+
+// Sum of N 16-byte pieces of a row as two partial sums (a pairwise tree).
+template <int N>
+__device__ inline float2 add_row_quads(const float4* row) {
+  float2 h[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const float4 a = row[i];
+    h[i] = __fadd2_rn(make_float2(a.x, a.y), make_float2(a.z, a.w));
+  }
+#pragma unroll
+  for (int w = N / 2; w > 0; w >>= 1)
+#pragma unroll
+    for (int i = 0; i < w; ++i) h[i] = __fadd2_rn(h[i], h[i + w]);
+  return h[0];
+}
+
+__device__ inline float reduce_rows16(const float* __restrict__ red) {
+  const int lane = threadIdx.x & 31;
   const float4* row = reinterpret_cast<const float4*>(red + (lane >> 1) * kRedStride + (lane & 1) * 16);
-  const float4 a = row[0], b = row[1], c = row[2], d = row[3];
-  float2 acc = __fadd2_rn(make_float2(a.x, a.y), make_float2(a.z, a.w));
-  acc = __fadd2_rn(acc, __fadd2_rn(make_float2(b.x, b.y), make_float2(b.z, b.w)));
-  acc = __fadd2_rn(acc, __fadd2_rn(make_float2(c.x, c.y), make_float2(c.z, c.w)));
-  acc = __fadd2_rn(acc, __fadd2_rn(make_float2(d.x, d.y), make_float2(d.z, d.w)));
-  __syncwarp();   // the scratch is rewritten by the next call
+  const float2 acc = add_row_quads<4>(row);
   const float r = acc.x + acc.y;
   return r + __shfl_xor_sync(kFull, r, 1);
+}
+
+__device__ inline float reduce_rows32(const float* __restrict__ red) {
+  const int lane = threadIdx.x & 31;
+  const float2 acc = add_row_quads<8>(reinterpret_cast<const float4*>(red + lane * kRedStride));
+  return acc.x + acc.y;
 }
 
 // One backward work item (same decomposition as fwd_item): the warp replays
@@ -380,15 +402,14 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       my[3][lane] = __ldg(r + 3);
       my_e[lane] = e;
     }
-    unsigned m = wm;
     __syncwarp();
-    while (m) {
-      const int j = 31 - __clz(m);     // back to front
-      m &= ~(1u << j);
+    // One visit: the splat's gradient at this lane's pixel, stored as 16 rows
+    // of the reduction scratch.  Branch-free: every lane evaluates the splat;
+    // lanes that do not blend it (behind their last contributor, or alpha below
+    // alpha_min) take alpha = 0, which leaves T and the running sums unchanged
+    // and zeroes every gradient.
+    auto visit = [&](int j, float* rows) {
       const int idx = c0 + j;
-      // Branch-free: every lane evaluates the splat; lanes that do not blend it
-      // (behind their last contributor, or alpha below alpha_min) take alpha = 0,
-      // which leaves T and the running sums unchanged and zeroes every gradient.
       // gradient slots as pairs: (U,V) (CA,CB) (CC,O) (CUT,Z) (P0,P1) (N0,N1) (N2,R) (G,B)
       float2 gr[8];
       const bool live = idx <= last;
@@ -438,15 +459,37 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       // (a dx + b dy, b dx + c dy)
       const float2 mm = __ffma2_rn(make_float2(a.z, a.w), make_float2(dx, dx),
                                    __fmul2_rn(make_float2(a.w, b.x), make_float2(dy, dy)));
-      const float2 guv = __ffma2_rn(make_float2(gs, gs), mm, __fmul2_rn(make_float2(sd, sd),
-                                                                          make_float2(e2.x, e2.y)));
-      gr[0] = guv;
-      // some lane blends every replayed record (the forward's mask), so every
-      // visit reduces
-      const float s = warp_reduce_scatter16(gr, my_red);
-      const int slot = lane >> 1;
-      if ((lane & 1) == 0 && slot != R_CUT && s != 0.f)
-        atomicAdd(grad + (int64_t)my_e[j] * kRecFloats + slot, s);
+      gr[0] = __ffma2_rn(make_float2(gs, gs), mm, __fmul2_rn(make_float2(sd, sd), make_float2(e2.x, e2.y)));
+      store_rows16(gr, rows);
+    };
+    // some lane blends every replayed record (the forward's mask), so every
+    // visit reduces.  Records go back to front, two per round where possible:
+    // their evaluations overlap and one reduction and one atomic instruction
+    // serve both.
+    unsigned m = wm;
+    while (m) {
+      const int jA = 31 - __clz(m);
+      m &= ~(1u << jA);
+      if (m == 0) {
+        visit(jA, my_red);
+        __syncwarp();
+        const float s = reduce_rows16(my_red);
+        __syncwarp();   // the scratch is rewritten by the next visit
+        const int slot = lane >> 1;
+        if ((lane & 1) == 0 && slot != R_CUT && s != 0.f)
+          atomicAdd(grad + (int64_t)my_e[jA] * kRecFloats + slot, s);
+        break;
+      }
+      const int jB = 31 - __clz(m);
+      m &= ~(1u << jB);
+      visit(jA, my_red);
+      visit(jB, my_red + 16 * kRedStride);
+      __syncwarp();
+      const float s = reduce_rows32(my_red);
+      __syncwarp();
+      const int slot = lane & 15;
+      if (slot != R_CUT && s != 0.f)
+        atomicAdd(grad + (int64_t)my_e[lane < 16 ? jA : jB] * kRecFloats + slot, s);
     }
     __syncwarp();
   }
@@ -489,7 +532,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
              int n_items) {
   __shared__ float4 s_rec[kRenderThreads / 32][4][32];
   __shared__ uint32_t s_ent[kRenderThreads / 32][32];
-  __shared__ __align__(16) float s_red[kRenderThreads / 32][16 * kRedStride];
+  __shared__ __align__(16) float s_red[kRenderThreads / 32][32 * kRedStride];
   Header* hdr = at<Header>(ws, L.hdr);
   BwdCounters* bc = at<BwdCounters>(ws, L.bwdcnt);
   if (hdr->status == GS_ERR_CAPACITY) return;
