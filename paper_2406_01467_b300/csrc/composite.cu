@@ -213,8 +213,8 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       cm |= 1u << j;
       const float w = al * T;
       const float4 e2 = my[2][j], e3 = my[3][j];
-      if (!GEO) { C0 += w * e3.y; C1 += w * e3.z; C2 += w * e3.w; }
-      N0 += w * e2.z; N1 += w * e2.w; N2 += w * e3.x;
+      if (!GEO) { C0 += w * e3.x; C1 += w * e3.y; C2 += w * e3.z; }
+      N0 += w * e3.w; N1 += w * e2.z; N2 += w * e2.w;
       const float dk = b.w + e2.x * dx + e2.y * dy;   // Eq. 4
       if (LOSS) {
         if (last < 0) d0 = dk;
@@ -384,7 +384,6 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
   // running "behind" sums of (r, g, b, n0, n1, n2) and the upstream of the same six, as pairs
   float2 S01 = make_float2(0.f, 0.f), S23 = make_float2(0.f, 0.f), S45 = make_float2(0.f, 0.f);
   const float2 U01 = make_float2(dC[0], dC[1]), U23 = make_float2(dC[2], dN[0]), U45 = make_float2(dN[1], dN[2]);
-  const float2 dN01 = make_float2(dN[0], dN[1]), dN2C0 = make_float2(dN[2], dC[0]), dC12 = make_float2(dC[1], dC[2]);
   const float2 nfp = make_float2(-fpx, -fpy);
   // the forward's per-chunk masks name the records some lane of this block
   // blended; the others have zero gradient here and are not replayed
@@ -410,10 +409,9 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
     // and zeroes every gradient.
     auto visit = [&](int j, float* rows) {
       const int idx = c0 + j;
-      // gradient slots as pairs: (U,V) (CA,CB) (CC,O) (CUT,Z) (P0,P1) (N0,N1) (N2,R) (G,B)
+      // gradient slots as pairs: (U,V) (CA,CB) (CC,O) (CUT,Z) (P0,P1) (N1,N2) (R,G) (B,N0)
       float2 gr[8];
       const bool live = idx <= last;
-      evals += live ? 1u : 0u;
       const float4 a = my[0][j], b = my[1][j], e2 = my[2][j], e3 = my[3][j];
       const float2 d = __fadd2_rn(make_float2(a.x, a.y), nfp);     // (dx, dy)
       const float dx = d.x, dy = d.y;
@@ -429,10 +427,10 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float w = al * T;
       const float2 w2 = make_float2(w, w);
       // colour and normal: (rgb, n) and the upstream (dC, dN) as three pairs
-      const float2 x0 = make_float2(e3.y, e3.z), x1 = make_float2(e3.w, e2.z), x2 = make_float2(e2.w, e3.x);
-      gr[5] = __fmul2_rn(w2, dN01);
-      gr[6] = __fmul2_rn(w2, dN2C0);
-      gr[7] = __fmul2_rn(w2, dC12);
+      const float2 x0 = make_float2(e3.x, e3.y), x1 = make_float2(e3.z, e3.w), x2 = make_float2(e2.z, e2.w);
+      gr[5] = __fmul2_rn(w2, U45);
+      gr[6] = __fmul2_rn(w2, U01);
+      gr[7] = __fmul2_rn(w2, U23);
       // (x - S) enters both dL/dalpha and the update S += alpha (x - S)
       const float2 q0 = __fadd2_rn(x0, make_float2(-S01.x, -S01.y));
       const float2 q1 = __fadd2_rn(x1, make_float2(-S23.x, -S23.y));
@@ -466,6 +464,10 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
     // visit reduces.  Records go back to front, two per round where possible:
     // their evaluations overlap and one reduction and one atomic instruction
     // serve both.
+    {   // evaluations of this lane: replayed records at or before its last contributor
+      const int lj = last - c0;
+      evals += lj < 0 ? 0u : __popc(lj >= 31 ? wm : wm & ((2u << lj) - 1u));
+    }
     unsigned m = wm;
     while (m) {
       const int jA = 31 - __clz(m);

@@ -24,8 +24,8 @@ constexpr int kRadix = 1 << kRadixBits;
 enum RecSlot {
   R_U = 0, R_V = 1, R_CA = 2, R_CB = 3,      // float4 #0: centre, conic a b
   R_CC = 4, R_O = 5, R_CUT = 6, R_Z = 7,     // float4 #1: conic c, opacity, sigma cut, z_c
-  R_P0 = 8, R_P1 = 9, R_N0 = 10, R_N1 = 11,  // float4 #2: depth plane p, normal
-  R_N2 = 12, R_R = 13, R_G = 14, R_B = 15    // float4 #3: normal, colour
+  R_P0 = 8, R_P1 = 9, R_N1 = 10, R_N2 = 11,  // float4 #2: depth plane p, normal y z
+  R_R = 12, R_G = 13, R_B = 14, R_N0 = 15    // float4 #3: colour, normal x
 };
 
 struct ViewDev {

@@ -432,8 +432,8 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
       const float cut = logf(o / amin) * 1.0001f + 1e-4f;
       r[0] = make_float4(u, v, conic[0], conic[1]);
       r[1] = make_float4(conic[2], o, cut, z);
-      r[2] = make_float4(pp[0], pp[1], nn[0], nn[1]);
-      r[3] = make_float4(nn[2], rgb[0], rgb[1], rgb[2]);
+      r[2] = make_float4(pp[0], pp[1], nn[1], nn[2]);
+      r[3] = make_float4(rgb[0], rgb[1], rgb[2], nn[0]);
       rect[e] = make_short4((short)i0, (short)i1, (short)j0, (short)j1);
       key[e] = __float_as_uint(z);
       touched[e] = (uint32_t)(((i1 >> sx) - (i0 >> sx) + 1) * ((j1 >> sy) - (j0 >> sy) + 1));
@@ -507,8 +507,8 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
       // record holds 0 for it
       {
         const float4 rgbf = rec4[4 * e + 3], grgb4 = g2d[4 * e + 3];
-        const float gval[3] = {rgbf.y > 0.f ? grgb4.y : 0.f, rgbf.z > 0.f ? grgb4.z : 0.f,
-                               rgbf.w > 0.f ? grgb4.w : 0.f};
+        const float gval[3] = {rgbf.x > 0.f ? grgb4.x : 0.f, rgbf.y > 0.f ? grgb4.y : 0.f,
+                               rgbf.z > 0.f ? grgb4.z : 0.f};
         const float d[3] = {m[0] - V.campos[0], m[1] - V.campos[1], m[2] - V.campos[2]};
         const float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         const float dir[3] = {d[0] * il, d[1] * il, d[2] * il};
@@ -548,7 +548,7 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
       const float gu = ga.x, gv = ga.y, gca = ga.z, gcb = ga.w;
       const float gcc = gb4.x, gz = gb4.w;
       go = gb4.y;
-      const float gp0 = gc4.x, gp1 = gc4.y, gn[3] = {gc4.z, gc4.w, gd4.x};
+      const float gp0 = gc4.x, gp1 = gc4.y, gn[3] = {gd4.w, gc4.z, gc4.w};
 
       // ---- p = (z/t) q -----------------------------------------------------------
       const float it = 1.f / gg.tc;

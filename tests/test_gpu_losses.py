@@ -154,7 +154,7 @@ def test_loss_gradients_match_oracle(which):
     torch.cuda.synchronize()
     dbg = fr.debug()["grad2d"].cpu().numpy()
     cols = {"u": [0], "v": [1], "conic": [2, 3, 4], "opacity": [5], "z": [7], "p": [8, 9],
-            "n": [10, 11, 12], "rgb": [13, 14, 15]}
+            "n": [15, 10, 11], "rgb": [12, 13, 14]}
     g2_gpu = {k: dbg[:, c].reshape(g2[k].shape) for k, c in cols.items()}
     rep2 = _grad_rep(g2_gpu, {k: g2[k] for k in cols})
     rep = _grad_rep({k: g.cpu().numpy() for k, g in grads.items()}, pg)

@@ -62,8 +62,8 @@ def test_records_match_oracle_tiny():
     np.testing.assert_allclose(rec[v, 5], pre["opacity"][v], rtol=1e-7)
     np.testing.assert_allclose(rec[v, 7], pre["z"][v], rtol=1e-6)
     np.testing.assert_allclose(rec[v, 8:10], pre["p"][v], atol=1e-5)
-    np.testing.assert_allclose(rec[v, 10:13], pre["n"][v], atol=1e-5)
-    np.testing.assert_allclose(rec[v, 13:16], pre["rgb"][v], atol=1e-5)
+    np.testing.assert_allclose(rec[v][:, [15, 10, 11]], pre["n"][v], atol=1e-5)   # (n_x | p, n_y, n_z)
+    np.testing.assert_allclose(rec[v, 12:15], pre["rgb"][v], atol=1e-5)
     # the sigma cut bounds the alpha test: exp(-cut) * o <= alpha_min
     cut = rec[v, 6]
     assert (pre["opacity"][v] * np.exp(-cut.astype(np.float64)) <= np.float32(p.alpha_min)).all()
@@ -132,7 +132,7 @@ def test_backward_matches_oracle_tiny(tile):
     dbg = fr.debug()["grad2d"].cpu().numpy()
     v = ref_f["dec"]["valid"]
     cols = {"u": [0], "v": [1], "conic": [2, 3, 4], "opacity": [5], "z": [7], "p": [8, 9],
-            "n": [10, 11, 12], "rgb": [13, 14, 15]}
+            "n": [15, 10, 11], "rgb": [12, 13, 14]}
     g2_gpu = {k: dbg[v][:, c].reshape(g2[k][v].shape) for k, c in cols.items()}
     g2_ref = {k: g2[k][v] for k in cols}
     rep2 = _grad_compare(g2_gpu, g2_ref)
