@@ -276,54 +276,42 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   }
 }
 
-// Warp reductions of gradient rows.  Every lane stores its values into the
-// warp's shared scratch as rows red[slot][lane] (row stride kRedStride = 36
-// floats: the row stores and the 16-byte row loads below are both free of bank
-// conflicts), then lanes add rows.
-//  - 16 rows (one record): lane l adds row l >> 1 over one half of the warp
-//    with four 16-byte loads; lanes l, l^1 combine their halves, after which
-//    lane l holds the warp-wide sum of slot l >> 1.
-//  - 32 rows (two records): lane l adds all of row l with eight 16-byte loads
-//    and holds the sum of slot l & 15 of record l >> 4; no shuffle.
+// Warp reduction of the gradient slots of one or two records.  First lanes l
+// and l^16 fold their 16 values with shuffles: the lower lane keeps slots 0-7,
+// the upper one slots 8-15, each summed over both lanes.  The 8 values then go
+// to the warp's shared scratch as rows red[row][lane] (rows 0-7: record A,
+// 8-15: record B; stride kRedStride = 36 floats keeps the row stores and the
+// 16-byte loads free of bank conflicts), and lane l adds the half row holding
+// slot l & 15 of record l >> 4 with four 16-byte loads.  The shuffle fold
+// halves the shared-memory traffic of a transpose through shared memory.
 constexpr int kRedStride = 36;
 
-__device__ inline void store_rows16(const float2 (&v)[8], float* __restrict__ red) {
+__device__ inline void fold_store(const float2 (&g)[8], float* __restrict__ rows) {
   const int lane = threadIdx.x & 31;
+  const bool hi = lane & 16;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    red[(2 * k) * kRedStride + lane] = v[k].x;
-    red[(2 * k + 1) * kRedStride + lane] = v[k].y;
+  for (int k = 0; k < 4; ++k) {
+    const float2 send = hi ? g[k] : g[k + 4];
+    const float2 keep = hi ? g[k + 4] : g[k];
+    const float2 recv = make_float2(__shfl_xor_sync(kFull, send.x, 16), __shfl_xor_sync(kFull, send.y, 16));
+    const float2 h = __fadd2_rn(keep, recv);
+    rows[(2 * k) * kRedStride + lane] = h.x;
+    rows[(2 * k + 1) * kRedStride + lane] = h.y;
   }
 }
 
-// Sum of N 16-byte pieces of a row as two partial sums (a pairwise tree).
-template <int N>
-__device__ inline float2 add_row_quads(const float4* row) {
-  float2 h[N];
+__device__ inline float reduce_rows(const float* __restrict__ red) {
+  const int lane = threadIdx.x & 31, s = lane & 15;
+  const float4* q =
+      reinterpret_cast<const float4*>(red + ((lane >> 4) * 8 + (s & 7)) * kRedStride + (s >> 3) * 16);
+  float2 h[4];
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const float4 a = row[i];
+  for (int i = 0; i < 4; ++i) {
+    const float4 a = q[i];
     h[i] = __fadd2_rn(make_float2(a.x, a.y), make_float2(a.z, a.w));
   }
-#pragma unroll
-  for (int w = N / 2; w > 0; w >>= 1)
-#pragma unroll
-    for (int i = 0; i < w; ++i) h[i] = __fadd2_rn(h[i], h[i + w]);
-  return h[0];
-}
-
-__device__ inline float reduce_rows16(const float* __restrict__ red) {
-  const int lane = threadIdx.x & 31;
-  const float4* row = reinterpret_cast<const float4*>(red + (lane >> 1) * kRedStride + (lane & 1) * 16);
-  const float2 acc = add_row_quads<4>(row);
-  const float r = acc.x + acc.y;
-  return r + __shfl_xor_sync(kFull, r, 1);
-}
-
-__device__ inline float reduce_rows32(const float* __restrict__ red) {
-  const int lane = threadIdx.x & 31;
-  const float2 acc = add_row_quads<8>(reinterpret_cast<const float4*>(red + lane * kRedStride));
-  return acc.x + acc.y;
+  const float2 t = __fadd2_rn(__fadd2_rn(h[0], h[1]), __fadd2_rn(h[2], h[3]));
+  return t.x + t.y;
 }
 
 // One backward work item (same decomposition as fwd_item): the warp replays
@@ -458,7 +446,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float2 mm = __ffma2_rn(make_float2(a.z, a.w), make_float2(dx, dx),
                                    __fmul2_rn(make_float2(a.w, b.x), make_float2(dy, dy)));
       gr[0] = __ffma2_rn(make_float2(gs, gs), mm, __fmul2_rn(make_float2(sd, sd), make_float2(e2.x, e2.y)));
-      store_rows16(gr, rows);
+      fold_store(gr, rows);
     };
     // some lane blends every replayed record (the forward's mask), so every
     // visit reduces.  Records go back to front, two per round where possible:
@@ -472,26 +460,17 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
     while (m) {
       const int jA = 31 - __clz(m);
       m &= ~(1u << jA);
-      if (m == 0) {
-        visit(jA, my_red);
-        __syncwarp();
-        const float s = reduce_rows16(my_red);
-        __syncwarp();   // the scratch is rewritten by the next visit
-        const int slot = lane >> 1;
-        if ((lane & 1) == 0 && slot != R_CUT && s != 0.f)
-          atomicAdd(grad + (int64_t)my_e[jA] * kRecFloats + slot, s);
-        break;
-      }
-      const int jB = 31 - __clz(m);
-      m &= ~(1u << jB);
+      const int jB = m ? 31 - __clz(m) : -1;
       visit(jA, my_red);
-      visit(jB, my_red + 16 * kRedStride);
+      if (jB >= 0) {
+        m &= ~(1u << jB);
+        visit(jB, my_red + 8 * kRedStride);
+      }
       __syncwarp();
-      const float s = reduce_rows32(my_red);
-      __syncwarp();
-      const int slot = lane & 15;
-      if (slot != R_CUT && s != 0.f)
-        atomicAdd(grad + (int64_t)my_e[lane < 16 ? jA : jB] * kRecFloats + slot, s);
+      const float s = reduce_rows(my_red);   // lanes 16-31 read stale rows without jB
+      __syncwarp();   // the scratch is rewritten by the next round
+      const int slot = lane & 15, j = lane < 16 ? jA : jB;
+      if (j >= 0 && slot != R_CUT && s != 0.f) atomicAdd(grad + (int64_t)my_e[j] * kRecFloats + slot, s);
     }
     __syncwarp();
   }
@@ -534,7 +513,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
              int n_items) {
   __shared__ float4 s_rec[kRenderThreads / 32][4][32];
   __shared__ uint32_t s_ent[kRenderThreads / 32][32];
-  __shared__ __align__(16) float s_red[kRenderThreads / 32][32 * kRedStride];
+  __shared__ __align__(16) float s_red[kRenderThreads / 32][16 * kRedStride];
   Header* hdr = at<Header>(ws, L.hdr);
   BwdCounters* bc = at<BwdCounters>(ws, L.bwdcnt);
   if (hdr->status == GS_ERR_CAPACITY) return;
