@@ -241,7 +241,9 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
        int64_t n_chunks) {
   __shared__ uint32_t s_off[kEmitChunk + 1], s_ent[kEmitChunk + 1];
   __shared__ short4 s_rc[kEmitChunk + 1];
+  __shared__ uint4 s_idx[kEmitChunk / 8];   // per pair: its entry's slot in s_off (uint16, 8 per piece)
   __shared__ int64_t s_k[2];
+  static_assert(kEmitChunk == 8 * kSortThreads, "one 8-pair run per thread");
   const int64_t n = clamp_count(n_vis_ptr, E);
   const int64_t P = clamp_count(n_pairs_ptr, cap);
   const int nv = fd->n_views;
@@ -270,17 +272,38 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
       s_rc[i] = rect[e];
     }
     __syncthreads();
-    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-      int lo = 0, hi = m - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= (uint32_t)p) lo = mid; else hi = mid - 1;
+    // each thread finds the entry of its first of 8 consecutive pairs by
+    // binary search and walks forward for the other 7
+    {
+      const uint32_t q0 = (uint32_t)(p0 + 8 * threadIdx.x);
+      const int64_t left = p1 - (int64_t)q0;
+      const int np = left < 8 ? (int)left : 8;
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      if (np > 0) {
+        int lo = 0, hi = m - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= q0) lo = mid; else hi = mid - 1;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          if (r < np) {
+            while (lo + 1 < m && s_off[lo + 1] <= q0 + r) ++lo;
+            w[r >> 1] |= (uint32_t)lo << (16 * (r & 1));
+          }
+        }
       }
+      s_idx[threadIdx.x] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __syncthreads();
+    const uint16_t* idx = reinterpret_cast<const uint16_t*>(s_idx);
+    for (int i = threadIdx.x; i < (int)(p1 - p0); i += blockDim.x) {   // coalesced writes
+      const int lo = idx[i];
       const uint32_t e = s_ent[lo];
       const short4 rc = s_rc[lo];
       const int tx0 = rc.x >> sx, ty0 = rc.z >> sy;
       const uint32_t nx = (uint32_t)((rc.y >> sx) - tx0 + 1);
-      const uint32_t local = (uint32_t)p - s_off[lo];
+      const uint32_t local = (uint32_t)(p0 + i) - s_off[lo];
       const uint32_t ty = local / nx, tx = local - ty * nx;
       int rowlen = tiles_x0, toff = 0;
       if (nv > 1) {
@@ -288,8 +311,8 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
         rowlen = fd->views[vi].tiles_x;
         toff = fd->tile_off[vi];
       }
-      ptile[p] = (uint32_t)(toff + (ty0 + (int)ty) * rowlen + tx0 + (int)tx);
-      pval[p] = e;
+      ptile[p0 + i] = (uint32_t)(toff + (ty0 + (int)ty) * rowlen + tx0 + (int)tx);
+      pval[p0 + i] = e;
     }
   }
 }
