@@ -287,8 +287,11 @@ gs_status gs_adam_step(float* params, float* grads, float* m, float* v, int64_t 
  * (the sigma cut is ln(o / alpha_min) plus a margin: beyond it a splat cannot
  * reach alpha_min); rect: [n_entries][4] int32 pixel rectangle (i0, i1, j0, j1), (0,-1,0,-1)
  * when culled; pair_tile/pair_entry: [pair_capacity] int32 sorted pairs;
- * ranges: [total tiles][2] int32.  grad2d: [n_entries][16] FP32 dL/d(record),
- * valid after gs_render_bwd. */
+ * ranges: [total tiles][2] int32.  grad2d: [n_entries][16] FP32 per-entry sums
+ * of the compositing backward, valid after gs_render_bwd: with gs = dL/dsigma
+ * and sd = dL/dd per pixel, (S gs dx, S gs dy, S gs dx^2, S gs dx dy,
+ * S gs dy^2, S gs, 0, S sd, S sd dx, S sd dy) and dL/d(n1, n2, r, g, b, n0);
+ * dL/d(record) follows with the entry's conic, p and opacity. */
 gs_status gs_debug_copy(const gs_frame* frame, float* rec, int32_t* rect,
                         int32_t* pair_tile, int32_t* pair_entry, int32_t* ranges,
                         float* grad2d, void* stream);

@@ -397,7 +397,11 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
     // and zeroes every gradient.
     auto visit = [&](int j, float* rows) {
       const int idx = c0 + j;
-      // gradient slots as pairs: (U,V) (CA,CB) (CC,O) (CUT,Z) (P0,P1) (N1,N2) (R,G) (B,N0)
+      // slots as pairs: (U,V) (CA,CB) (CC,O) (CUT,Z) (P0,P1) (N1,N2) (R,G) (B,N0); the
+      // first seven hold sums that are linear in the splat's conic, p and o:
+      // (S gs dx, S gs dy) (S gs dx^2, S gs dx dy) (S gs dy^2, S gs) (0, S sd)
+      // (S sd dx, S sd dy), with gs = dL/dsigma and sd = dL/dd; the preprocess
+      // backward applies the constants once per entry
       float2 gr[8];
       const bool live = idx <= last;
       const float4 a = my[0][j], b = my[1][j], e2 = my[2][j], e3 = my[3][j];
@@ -436,16 +440,13 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       if (LOSS) sd += c4 * w * ((b.w + e2.x * dx + e2.y * dy) - dmean);
       gr[3] = make_float2(0.f, sd);
       gr[4] = __fmul2_rn(make_float2(sd, sd), d);
-      // alpha = o G below the clamp: opacity, conic and centre
+      // alpha = o G below the clamp: dL/dsigma = -dL/dalpha alpha
       const float gs = raw <= amax ? -dal * al : 0.f;
-      const float2 hgs = make_float2(0.5f * gs, 0.5f * gs);
-      const float2 cac = __fmul2_rn(hgs, d2);            // (CA, CC)
-      gr[1] = make_float2(cac.x, gs * dx * dy);          // (CA, CB)
-      gr[2] = make_float2(cac.y, raw <= amax ? dal * G : 0.f);   // (CC, O)
-      // (a dx + b dy, b dx + c dy)
-      const float2 mm = __ffma2_rn(make_float2(a.z, a.w), make_float2(dx, dx),
-                                   __fmul2_rn(make_float2(a.w, b.x), make_float2(dy, dy)));
-      gr[0] = __ffma2_rn(make_float2(gs, gs), mm, __fmul2_rn(make_float2(sd, sd), make_float2(e2.x, e2.y)));
+      const float2 gs2 = make_float2(gs, gs);
+      gr[0] = __fmul2_rn(gs2, d);
+      const float2 gq = __fmul2_rn(gs2, d2);
+      gr[1] = make_float2(gq.x, gr[0].x * dy);
+      gr[2] = make_float2(gq.y, gs);
       fold_store(gr, rows);
     };
     // some lane blends every replayed record (the forward's mask), so every

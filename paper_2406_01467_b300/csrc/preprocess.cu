@@ -545,9 +545,14 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
       geo_forward(V, m, s, q, lp, geo);
       const Geo& gg = geo;
       const float4 ga = g2d[4 * e], gb4 = g2d[4 * e + 1], gc4 = g2d[4 * e + 2], gd4 = g2d[4 * e + 3];
-      const float gu = ga.x, gv = ga.y, gca = ga.z, gcb = ga.w;
-      const float gcc = gb4.x, gz = gb4.w;
-      go = gb4.y;
+      // the compositing backward leaves sums linear in the conic, p and o:
+      // (S gs dx, S gs dy, S gs dx^2, S gs dx dy, S gs dy^2, S gs, -, S sd), gs = dL/dsigma;
+      // sigma = (c_a dx^2 + c_c dy^2) / 2 + c_b dx dy, alpha = o exp(-sigma), d = z + p . Delta
+      const float gz = gb4.w;
+      const float gu = gg.ca * ga.x + gg.cb * ga.y + gg.p0 * gz;
+      const float gv = gg.cb * ga.x + gg.cc * ga.y + gg.p1 * gz;
+      const float gca = 0.5f * ga.z, gcb = ga.w, gcc = 0.5f * gb4.x;
+      go = -gb4.y / o;
       const float gp0 = gc4.x, gp1 = gc4.y, gn[3] = {gd4.w, gc4.z, gc4.w};
 
       // ---- p = (z/t) q -----------------------------------------------------------

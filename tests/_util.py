@@ -53,3 +53,26 @@ def _same_ranges(got, ref):
     full = ref[:, 1] > ref[:, 0]
     np.testing.assert_array_equal(got[full], ref[full])
     assert (got[~full, 1] <= got[~full, 0]).all()
+
+
+def grad2d_to_record(g2d, pre):
+    """dL/d(record field) per entry from the GPU's per-entry 2D sums (the
+    `grad2d` debug buffer) and the entries' conic, p and opacity.  The
+    compositing backward accumulates sums that are linear in those constants:
+    columns (S gs dx, S gs dy, S gs dx^2, S gs dx dy, S gs dy^2, S gs, 0, S sd,
+    S sd dx, S sd dy, n1, n2, r, g, b, n0) with gs = dL/dsigma, sd = dL/dd."""
+    M = np.asarray(g2d, np.float64)
+    c = np.nan_to_num(np.asarray(pre["conic"], np.float64))
+    p = np.nan_to_num(np.asarray(pre["p"], np.float64))
+    o = np.asarray(pre["opacity"], np.float64)
+    safe_o = np.where(o > 0, o, 1.0)
+    return {
+        "u": c[:, 0] * M[:, 0] + c[:, 1] * M[:, 1] + p[:, 0] * M[:, 7],
+        "v": c[:, 1] * M[:, 0] + c[:, 2] * M[:, 1] + p[:, 1] * M[:, 7],
+        "conic": np.stack([0.5 * M[:, 2], M[:, 3], 0.5 * M[:, 4]], 1),
+        "opacity": np.where(o > 0, -M[:, 5] / safe_o, 0.0),
+        "z": M[:, 7],
+        "p": M[:, 8:10],
+        "n": M[:, [15, 10, 11]],
+        "rgb": M[:, 12:15],
+    }

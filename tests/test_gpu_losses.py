@@ -16,9 +16,10 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from oracle import losses as olosses
 from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, scenes
-from tests._util import AMBIG_MARGIN, compare_maps, gpu_maps_at, oracle_params
+from tests._util import AMBIG_MARGIN, compare_maps, gpu_maps_at, grad2d_to_record, oracle_params
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
@@ -153,10 +154,10 @@ def test_loss_gradients_match_oracle(which):
     grads = fr.backward(*t[:4], ddist=t[4], dnloss=t[5])[0]
     torch.cuda.synchronize()
     dbg = fr.debug()["grad2d"].cpu().numpy()
-    cols = {"u": [0], "v": [1], "conic": [2, 3, 4], "opacity": [5], "z": [7], "p": [8, 9],
-            "n": [15, 10, 11], "rgb": [12, 13, 14]}
-    g2_gpu = {k: dbg[:, c].reshape(g2[k].shape) for k, c in cols.items()}
-    rep2 = _grad_rep(g2_gpu, {k: g2[k] for k in cols})
+    pre = oracle.render(sc, cam, op, pixels=np.array([0]))["pre"]
+    rec = grad2d_to_record(dbg, pre)
+    g2_gpu = {k: rec[k].reshape(g2[k].shape) for k in rec}
+    rep2 = _grad_rep(g2_gpu, {k: g2[k] for k in rec})
     rep = _grad_rep({k: g.cpu().numpy() for k, g in grads.items()}, pg)
     for k, (emax, enorm) in rep2.items():
         if which == "dist" and k in ("conic", "opacity", "rgb", "n"):

@@ -12,7 +12,7 @@ import torch
 import oracle
 from oracle import binning
 from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, scenes
-from tests._util import _same_ranges, AMBIG_MARGIN, compare_maps, gpu_maps_at, oracle_params
+from tests._util import _same_ranges, AMBIG_MARGIN, compare_maps, gpu_maps_at, grad2d_to_record, oracle_params
 
 pytestmark = pytest.mark.gpu
 
@@ -128,13 +128,12 @@ def test_backward_matches_oracle_tiny(tile):
     ups = [torch.from_numpy(u).to(DEV) for u in up]
     grads = fr.backward(*ups)[0]
     torch.cuda.synchronize()
-    # per-Gaussian 2D gradients (what the compositing backward accumulates)
+    # per-Gaussian 2D gradients (from the sums the compositing backward accumulates)
     dbg = fr.debug()["grad2d"].cpu().numpy()
     v = ref_f["dec"]["valid"]
-    cols = {"u": [0], "v": [1], "conic": [2, 3, 4], "opacity": [5], "z": [7], "p": [8, 9],
-            "n": [15, 10, 11], "rgb": [12, 13, 14]}
-    g2_gpu = {k: dbg[v][:, c].reshape(g2[k][v].shape) for k, c in cols.items()}
-    g2_ref = {k: g2[k][v] for k in cols}
+    rec = grad2d_to_record(dbg[v], {k: ref_f["pre"][k][v] for k in ("conic", "p", "opacity")})
+    g2_gpu = {k: rec[k].reshape(g2[k][v].shape) for k in rec}
+    g2_ref = {k: g2[k][v] for k in rec}
     rep2 = _grad_compare(g2_gpu, g2_ref)
     for k, (emax, enorm) in rep2.items():
         assert emax < 1e-3 and enorm < 1e-3, (k, rep2)
