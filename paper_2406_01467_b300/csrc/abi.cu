@@ -173,9 +173,9 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   const int passes = (tile_sort_bits(T) + kRadixBits - 1) / kRadixBits;
   L.ptile_final = L.ptile[passes & 1];
   L.pval_final = L.pval[passes & 1];
-  // histograms + tickets, then 4 passes (depth) or the tile passes of look-back words
+  // histograms + tickets, then the look-back words of the 4 depth passes or of the tile passes
   L.sortaux_bytes[0] = 8192 + (size_t)4 * L.nb_E * kRadix * 8;
-  L.sortaux_bytes[1] = 8192 + (size_t)4 * L.nb_P * kRadix * 8;
+  L.sortaux_bytes[1] = 8192 + (size_t)passes * L.nb_P * kRadix * 8;
   L.sortaux[0] = take(L.sortaux_bytes[0]);   // these three regions are contiguous:
   L.sortaux[1] = take(L.sortaux_bytes[1]);   // binning clears them with one memset
   L.ranges = take(8 * (size_t)T);
