@@ -162,7 +162,8 @@ def launches_per_step(n_tiles, n_dtypes=1):
     pair_scan = 2 + 1 + 1             # block sums, scan of partials, pair offsets, emission
     tile_sort = 1 + tile_passes       # digit histogram + one-sweep passes
     binning = compaction + depth_sort + pair_scan + tile_sort + 1 + 1   # ranges, work order
-    return setup + pre + binning + 1 + 1 + n_dtypes   # render fwd, composite bwd, preprocess bwd
+    # render fwd; backward clear of the visible 2D-gradient rows, composite bwd, preprocess bwd
+    return setup + pre + binning + 1 + 2 + n_dtypes
 
 
 # --------------------------------------------------------------------------------------

@@ -184,7 +184,7 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   L.px_T = take(bwd_state ? 4 * (size_t)NPIX : 0);
   L.px_last = take(bwd_state ? 4 * (size_t)NPIX : 0);
   L.px_med = take(bwd_state ? 4 * (size_t)NPIX : 0);
-  L.bwdcnt = take(bwd_state ? 256 : 0);       // contiguous with grad2d: one memset clears both
+  L.bwdcnt = take(bwd_state ? 256 : 0);
   L.grad2d = take(bwd_state ? 64 * (size_t)E : 0);
   L.px_loss = take(p.losses ? 4 * (size_t)kLossPlanes * NPIX : 0);
   // chunk k of tile t's list, 8x4 block b: word b * cmask_words + (start_t >> 5) + t + k;
@@ -228,6 +228,14 @@ __global__ void k_debug_rect(const short4* rect, int64_t E, int4* out) {
     short4 r = rect[i];
     out[i] = make_int4(r.x, r.y, r.z, r.w);
   }
+}
+
+// The backward clears only the visible entries' 2D-gradient rows: a culled
+// entry's row may hold an earlier frame's values, which the copy shows as 0.
+__global__ void k_debug_grad2d(const float4* src, const uint32_t* key, int64_t E, float4* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 4 * E;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = key[i >> 2] == kInvalidKey ? make_float4(0.f, 0.f, 0.f, 0.f) : src[i];
 }
 
 }  // namespace gs
@@ -378,7 +386,12 @@ gs_status gs_debug_copy(const gs_frame* frame, float* rec, int32_t* rect, int32_
   cp(pair_tile, L.ptile_final, 4 * (size_t)L.Pcap);
   cp(pair_entry, L.pval_final, 4 * (size_t)L.Pcap);
   cp(ranges, L.ranges, 8 * (size_t)L.T);
-  cp(grad2d, L.grad2d, 64 * (size_t)L.E);
+  if (e == cudaSuccess && grad2d && L.E > 0) {
+    int g = (int)std::min<int64_t>((4 * L.E + 255) / 256, 4096);
+    k_debug_grad2d<<<g, 256, 0, s>>>(at<float4>(ws, L.grad2d), at<uint32_t>(ws, L.key), L.E,
+                                     reinterpret_cast<float4*>(grad2d));
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess && rect && L.E > 0) {
     int g = (int)std::min<int64_t>((L.E + 255) / 256, 4096);
     k_debug_rect<<<g, 256, 0, s>>>(at<short4>(ws, L.rect), L.E, reinterpret_cast<int4*>(rect));

@@ -23,11 +23,6 @@ namespace gs {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
-__device__ inline int64_t clamp_count(const unsigned long long* p, int64_t cap) {
-  unsigned long long c = *p;
-  return (int64_t)(c < (unsigned long long)cap ? c : (unsigned long long)cap);
-}
-
 __device__ inline unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -570,14 +570,32 @@ cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& hf, con
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(256)
+k_bwd_clear(const uint32_t* __restrict__ vis, const unsigned long long* n_vis_ptr, int64_t E,
+            float4* __restrict__ grad2d, BwdCounters* bc) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    bc->n_evals_bwd = 0;
+    bc->work_bwd = 0;
+  }
+  const int64_t n = clamp_count(n_vis_ptr, E);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 4 * n; i += (int64_t)gridDim.x * blockDim.x)
+    grad2d[4 * (int64_t)vis[i >> 2] + (i & 3)] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& hf, const gs_map_grads& g,
                               cudaStream_t s) {
   const FrameDev* fd = at<FrameDev>(ws, L.frame);
   Header* hdr = at<Header>(ws, L.hdr);
-  // the backward counters and the 2D gradients are contiguous: one memset
-  cudaError_t err = cudaMemsetAsync(at<char>(ws, L.bwdcnt), 0,
-                                    L.grad2d + sizeof(float) * kRecFloats * (size_t)L.E - L.bwdcnt, s);
-  if (err != cudaSuccess) return err;
+  // zero the backward counters and the 2D-gradient rows of the visible entries
+  // (the only rows the compositing accumulates into and the preprocess
+  // backward reads), 4 threads per 64-byte row
+  {
+    const int g = (int)std::min<int64_t>(std::max<int64_t>((4 * L.E + 255) / 256, 1), 148 * 16);
+    k_bwd_clear<<<g, 256, 0, s>>>(at<uint32_t>(ws, L.vval[0]), &hdr->n_vis, L.E, at<float4>(ws, L.grad2d),
+                                  at<BwdCounters>(ws, L.bwdcnt));
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
   if (L.T == 0) return cudaSuccess;
   const int subs = hf.tile_w * hf.tile_h / 32;
   const int n_items = (int)L.T * subs;

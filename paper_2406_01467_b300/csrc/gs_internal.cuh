@@ -104,6 +104,12 @@ struct GradPtrs {
   gs_scene_grads g[GS_MAX_SCENES];
 };
 
+// A device-side count, clamped to the capacity it was computed against.
+__device__ inline int64_t clamp_count(const unsigned long long* p, int64_t cap) {
+  unsigned long long c = *p;
+  return (int64_t)(c < (unsigned long long)cap ? c : (unsigned long long)cap);
+}
+
 struct Header {
   unsigned long long n_vis;
   unsigned long long n_pairs;
