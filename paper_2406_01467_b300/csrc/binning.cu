@@ -441,18 +441,29 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   if (base >= n) return;   // so do all blocks with later tickets: nobody waits for this one
   uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
   const unsigned lt = lanemask_lt();
+  // tile-local item index of round r: w * 512 + 32 r + lane (WarpItems order)
+  const int nloc = (int)min((int64_t)kSortTile, n - base);
+  const int li0 = w * (32 * kSortItems) + (threadIdx.x & 31);
+  const uint32_t* kb = kin + base;
+  const uint32_t* vb = vin + base;
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {   // all loads in flight before any ranking
-    const int64_t i = WarpItems::index(base, r);
-    k[r] = i < n ? __ldg(kin + i) : 0u;
-    v[r] = i < n ? __ldg(vin + i) : 0u;
+    const int li = li0 + 32 * r;
+    k[r] = li < nloc ? __ldg(kb + li) : 0u;
+    v[r] = li < nloc ? __ldg(vb + li) : 0u;
+  }
+  // the peer masks of all items first (independent of one another), then the
+  // warp's running digit counts item by item
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int d = li0 + 32 * r < nloc ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
+    // a digit shared by the whole warp needs no matching
+    rank[r] = __all_sync(FULL, d == __shfl_sync(FULL, d, 0)) ? FULL : __match_any_sync(FULL, d);
   }
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    const bool ok = WarpItems::index(base, r) < n;
-    const int d = ok ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
-    // a digit shared by the whole warp needs no matching
-    const unsigned peers = __all_sync(FULL, d == __shfl_sync(FULL, d, 0)) ? FULL : __match_any_sync(FULL, d);
+    const int d = li0 + 32 * r < nloc ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
+    const unsigned peers = rank[r];
     const uint32_t old = d < kRadix ? s_wcnt[w][d] : 0u;
     rank[r] = old + __popc(peers & lt);
     __syncwarp();
@@ -492,8 +503,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   s_gbase[d] = dbase + excl;
   __syncthreads();
   for (int r = 0; r < kSortItems; ++r) {
-    const int64_t i = WarpItems::index(base, r);
-    if (i < n) {
+    if (li0 + 32 * r < nloc) {
       const int dd = (int)((k[r] >> shift) & (kRadix - 1));
       const uint32_t pos = s_wcnt[w][dd] + rank[r];
       s_keys[pos] = k[r];
@@ -501,7 +511,6 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
     }
   }
   __syncthreads();
-  const int nloc = (int)min((int64_t)kSortTile, n - base);
   for (int i = threadIdx.x; i < nloc; i += kSortThreads) {
     const uint32_t kk = s_keys[i];
     const int dd = (int)((kk >> shift) & (kRadix - 1));
