@@ -158,9 +158,9 @@ def launches_per_step(n_tiles, n_dtypes=1):
     tile_passes = (bits + 7) // 8
     setup, pre = 1, n_dtypes
     compaction = 3                    # block sums, scan of partials, compact
-    depth_sort = 1 + 4                # digit histogram + 4 one-sweep passes
+    depth_sort = 4                    # one-sweep passes (the compaction counts their digits)
     pair_scan = 2 + 1 + 1             # block sums, scan of partials, pair offsets, emission
-    tile_sort = 1 + tile_passes       # digit histogram + one-sweep passes
+    tile_sort = tile_passes           # one-sweep passes (the emission counts their digits)
     binning = compaction + depth_sort + pair_scan + tile_sort + 1 + 1   # ranges, work order
     # render fwd; backward clear of the visible 2D-gradient rows, composite bwd, preprocess bwd
     return setup + pre + binning + 1 + 2 + n_dtypes

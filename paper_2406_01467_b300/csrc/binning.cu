@@ -12,9 +12,9 @@
 //      list is then in (depth, entry) order, the same order as a full sort on
 //      (tile, depth bits, entry) keys;
 //   6. [start, end) of each tile.
-// The radix sort is one-sweep: one histogram kernel for all passes, then one
-// kernel per pass whose blocks chain their digit offsets by decoupled look-back
-// (bounded waits).
+// The radix sort is one-sweep: the kernel that writes the keys (compaction,
+// emission) also counts the digits of every pass, then one kernel per pass
+// whose blocks chain their digit offsets by decoupled look-back (bounded waits).
 #include <algorithm>
 
 #include "gs_internal.cuh"
@@ -27,6 +27,35 @@ __device__ inline unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
+}
+
+constexpr int kMaxPasses = 4;
+
+// Digit histograms of the radix sort's passes, accumulated by the kernel that
+// writes the keys: h[pass][digit] in shared memory, then added to the global
+// histograms.  Warp-collective (all 32 lanes call it): a digit shared by all of
+// the warp's valid keys (the high digits mostly are) costs one atomic.
+__device__ inline void hist_keys(uint32_t (*h)[kRadix], int passes, uint32_t key, bool valid) {
+  const unsigned vm = __ballot_sync(FULL, valid);
+  if (vm == 0) return;
+  const int leader = __ffs(vm) - 1;
+  for (int p = 0; p < passes; ++p) {
+    const int d = (int)((key >> (kRadixBits * p)) & (kRadix - 1));
+    const int d0 = __shfl_sync(FULL, d, leader);
+    if (__all_sync(FULL, !valid || d == d0)) {
+      if ((int)(threadIdx.x & 31) == leader) atomicAdd(&h[p][d0], (uint32_t)__popc(vm));
+    } else if (valid) {
+      atomicAdd(&h[p][d], 1u);
+    }
+  }
+}
+
+__device__ inline void hist_flush(uint32_t (*h)[kRadix], int passes, uint32_t* __restrict__ ghist) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+    const uint32_t c = (&h[0][0])[i];
+    if (c) atomicAdd(ghist + i, c);
+  }
 }
 
 // Block-wide exclusive scan of one uint32 per thread (256 threads).
@@ -135,8 +164,10 @@ struct WarpItems {
 // Compaction of visible entries: (key, entry) at their rank among visible ones.
 __global__ void __launch_bounds__(kSortThreads)
 k_compact(const uint32_t* __restrict__ key, int64_t E, const uint32_t* __restrict__ blk,
-          uint32_t* __restrict__ okey, uint32_t* __restrict__ oval) {
+          uint32_t* __restrict__ okey, uint32_t* __restrict__ oval, uint32_t* __restrict__ ghist) {
   __shared__ uint32_t s_wtot[8];
+  __shared__ uint32_t s_h[kMaxPasses][kRadix];   // the depth sort's digit histograms
+  for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   uint32_t k[kSortItems];
@@ -159,7 +190,9 @@ k_compact(const uint32_t* __restrict__ key, int64_t E, const uint32_t* __restric
       oval[pos] = (uint32_t)WarpItems::index(base, r);
     }
     off += __popc(bal);
+    hist_keys(s_h, kMaxPasses, k[r], v);
   }
+  hist_flush(s_h, kMaxPasses, ghist);
 }
 
 // Global exclusive scan of tiles_touched in depth order: pair_off[k] is the
@@ -233,12 +266,14 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
        const unsigned long long* n_vis_ptr, const unsigned long long* n_pairs_ptr, int64_t E,
        const short4* __restrict__ rect, const uint32_t* __restrict__ pair_off, int64_t cap,
        uint32_t* __restrict__ ptile, uint32_t* __restrict__ pval, const uint32_t* __restrict__ chunk_first,
-       int64_t n_chunks) {
+       int64_t n_chunks, int tile_passes, uint32_t* __restrict__ ghist) {
   __shared__ uint32_t s_off[kEmitChunk + 1], s_ent[kEmitChunk + 1];
   __shared__ short4 s_rc[kEmitChunk + 1];
   __shared__ uint4 s_idx[kEmitChunk / 8];   // per pair: its entry's slot in s_off (uint16, 8 per piece)
   __shared__ int64_t s_k[2];
+  __shared__ uint32_t s_h[kMaxPasses][kRadix];   // the tile sort's digit histograms
   static_assert(kEmitChunk == 8 * kSortThreads, "one 8-pair run per thread");
+  for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
   const int64_t n = clamp_count(n_vis_ptr, E);
   const int64_t P = clamp_count(n_pairs_ptr, cap);
   const int nv = fd->n_views;
@@ -292,24 +327,33 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
     }
     __syncthreads();
     const uint16_t* idx = reinterpret_cast<const uint16_t*>(s_idx);
-    for (int i = threadIdx.x; i < (int)(p1 - p0); i += blockDim.x) {   // coalesced writes
-      const int lo = idx[i];
-      const uint32_t e = s_ent[lo];
-      const short4 rc = s_rc[lo];
-      const int tx0 = rc.x >> sx, ty0 = rc.z >> sy;
-      const uint32_t nx = (uint32_t)((rc.y >> sx) - tx0 + 1);
-      const uint32_t local = (uint32_t)(p0 + i) - s_off[lo];
-      const uint32_t ty = local / nx, tx = local - ty * nx;
-      int rowlen = tiles_x0, toff = 0;
-      if (nv > 1) {
-        const int vi = find_view(fd->entry_off, nv, (int64_t)e);
-        rowlen = fd->views[vi].tiles_x;
-        toff = fd->tile_off[vi];
+    const int cnt = (int)(p1 - p0);
+    for (int i0 = 0; i0 < cnt; i0 += blockDim.x) {   // coalesced writes; warp-uniform trip count
+      const int i = i0 + threadIdx.x;
+      const bool ok = i < cnt;
+      uint32_t t = 0;
+      if (ok) {
+        const int lo = idx[i];
+        const uint32_t e = s_ent[lo];
+        const short4 rc = s_rc[lo];
+        const int tx0 = rc.x >> sx, ty0 = rc.z >> sy;
+        const uint32_t nx = (uint32_t)((rc.y >> sx) - tx0 + 1);
+        const uint32_t local = (uint32_t)(p0 + i) - s_off[lo];
+        const uint32_t ty = local / nx, tx = local - ty * nx;
+        int rowlen = tiles_x0, toff = 0;
+        if (nv > 1) {
+          const int vi = find_view(fd->entry_off, nv, (int64_t)e);
+          rowlen = fd->views[vi].tiles_x;
+          toff = fd->tile_off[vi];
+        }
+        t = (uint32_t)(toff + (ty0 + (int)ty) * rowlen + tx0 + (int)tx);
+        ptile[p0 + i] = t;
+        pval[p0 + i] = e;
       }
-      ptile[p0 + i] = (uint32_t)(toff + (ty0 + (int)ty) * rowlen + tx0 + (int)tx);
-      pval[p0 + i] = e;
+      hist_keys(s_h, tile_passes, t, ok);
     }
   }
+  hist_flush(s_h, tile_passes, ghist);
 }
 
 // ---------------------------------------------------------------------------
@@ -367,8 +411,8 @@ cudaError_t launch_tile_order(void* ws, const Layout& L, const uint32_t* cost, i
 }
 
 // ---------------------------------------------------------------------------
-// One-sweep LSD radix sort: the digit histograms of every pass come from one
-// read of the keys (k_digit_hist); each pass is then a single kernel in which
+// One-sweep LSD radix sort: the digit histograms of every pass are counted by
+// the kernel that writes the keys (hist_keys); each pass is then a single kernel in which
 // a block ranks its 4096 keys, publishes its per-digit counts, finds the
 // counts of all blocks before it by decoupled look-back (each predecessor's
 // word holds its own count, flagged A, or the inclusive prefix, flagged P) and
@@ -376,7 +420,6 @@ cudaError_t launch_tile_order(void* ws, const Layout& L, const uint32_t* cost, i
 // counter), so a block only ever waits for blocks that are already running;
 // every wait is bounded and sets GS_ERR_TIMEOUT if it runs out.
 // ---------------------------------------------------------------------------
-constexpr int kMaxPasses = 4;
 constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62, kFlagMask = 3ull << 62;
 constexpr int kSpinLimit = 1 << 22;
 
@@ -387,36 +430,6 @@ __device__ inline unsigned long long ld_relaxed(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
-}
-
-__global__ void __launch_bounds__(kSortThreads)
-k_digit_hist(const uint32_t* __restrict__ kin, const unsigned long long* count_ptr, int64_t cap, int passes,
-             uint32_t* __restrict__ ghist) {
-  __shared__ uint32_t s_h[kMaxPasses][kRadix];
-  for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kSortThreads) (&s_h[0][0])[i] = 0;
-  __syncthreads();
-  const int64_t n = clamp_count(count_ptr, cap);
-  const int64_t step = (int64_t)gridDim.x * kSortThreads;
-  for (int64_t i0 = (int64_t)blockIdx.x * kSortThreads; i0 < n; i0 += step) {   // warp-uniform loop
-    const int64_t i = i0 + threadIdx.x;
-    const uint32_t k = i < n ? __ldg(kin + i) : 0u;
-    const unsigned inb = __ballot_sync(FULL, i < n);
-    for (int p = 0; p < passes; ++p) {
-      const int d = (int)((k >> (kRadixBits * p)) & (kRadix - 1));
-      // a digit shared by the whole warp (the high digits mostly are) costs one
-      // atomic; otherwise each lane adds its own (mostly distinct low digits)
-      if (__all_sync(FULL, d == __shfl_sync(FULL, d, 0) || i >= n)) {
-        if ((threadIdx.x & 31) == __ffs(inb) - 1) atomicAdd(&s_h[p][d], __popc(inb));
-      } else if (i < n) {
-        atomicAdd(&s_h[p][d], 1u);
-      }
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) {
-    const uint32_t c = (&s_h[0][0])[i];
-    if (c) atomicAdd(ghist + i, c);
-  }
 }
 
 __global__ void __launch_bounds__(kSortThreads, 3)
@@ -520,8 +533,9 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   }
 }
 
-// Sorts (k0, v0) by the low `bits` bits of the keys; the result ends in
-// (k0, v0) after an even number of 8-bit passes, else in (k1, v1).
+// Sorts (k0, v0) by the low `bits` bits of the keys, whose digit histograms are
+// already in aux; the result ends in (k0, v0) after an even number of 8-bit
+// passes, else in (k1, v1).
 static cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                               const unsigned long long* count, int64_t cap, int nb, int bits, void* aux,
                               size_t aux_bytes, Header* hdr, cudaStream_t s) {
@@ -530,7 +544,6 @@ static cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t
   int* tickets = reinterpret_cast<int*>(ghist + kMaxPasses * kRadix);   // [kMaxPasses]
   unsigned long long* look = reinterpret_cast<unsigned long long*>(static_cast<char*>(aux) + 8192);
   (void)aux_bytes;   // cleared by the binning's single memset
-  k_digit_hist<<<std::min(nb, 148 * 8), kSortThreads, 0, s>>>(k0, count, cap, passes, ghist);
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
   for (int p = 0; p < passes; ++p) {
     k_onesweep<<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, cap, p, ghist, look + (int64_t)p * nb * kRadix,
@@ -565,7 +578,8 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   // 1. compaction
   k_block_sums<0><<<L.nb_E, kSortThreads, 0, s>>>(key, nullptr, nullptr, L.E, blk);
   k_scan_partials<<<1, 1024, 0, s>>>(blk, L.nb_E, &hdr->n_vis, 0, hdr);
-  k_compact<<<L.nb_E, kSortThreads, 0, s>>>(key, L.E, blk, vk0, vv0);
+  // (the compaction also counts the depth keys' digits for the sort)
+  k_compact<<<L.nb_E, kSortThreads, 0, s>>>(key, L.E, blk, vk0, vv0, at<uint32_t>(ws, L.sortaux[0]));
   // 2. depth sort: 31 bits (z > 0, so the sign bit is clear)
   cudaError_t err = radix_sort(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, at<void>(ws, L.sortaux[0]),
                                L.sortaux_bytes[0], hdr, s);
@@ -579,11 +593,14 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   const int64_t n_chunks = (L.Pcap + kEmitChunk - 1) / kEmitChunk + 1;
   k_pair_offsets<<<L.nb_E, kSortThreads, 0, s>>>(vv0, &hdr->n_vis, L.E, touched, blk, pair_off, chunk_first,
                                                   n_chunks);
+  // (the emission also counts the tile keys' digits for the sort)
+  const int bits = tile_sort_bits(L.T);
+  const int tile_passes = (bits + kRadixBits - 1) / kRadixBits;
   const int eg = (int)std::min<int64_t>((L.Pcap + kEmitChunk - 1) / kEmitChunk, 148 * 8);
   k_emit<<<eg, kSortThreads, 0, s>>>(fd, vv0, &hdr->n_vis, &hdr->n_pairs, L.E, at<short4>(ws, L.rect),
-                                     pair_off, L.Pcap, pt0, pv0, chunk_first, n_chunks);
+                                     pair_off, L.Pcap, pt0, pv0, chunk_first, n_chunks, tile_passes,
+                                     at<uint32_t>(ws, L.sortaux[1]));
   // 5. tile sort
-  const int bits = tile_sort_bits(L.T);
   err = radix_sort(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, at<void>(ws, L.sortaux[1]),
                    L.sortaux_bytes[1], hdr, s);
   if (err != cudaSuccess) return err;
