@@ -157,9 +157,9 @@ def launches_per_step(n_tiles, n_dtypes=1):
     bits = max(1, int(np.ceil(np.log2(max(n_tiles, 2)))))
     tile_passes = (bits + 7) // 8
     setup, pre = 1, n_dtypes
-    compaction = 3                    # block sums, scan of partials, compact
+    compaction = 1                    # one-pass compaction (look-back)
     depth_sort = 4                    # one-sweep passes (the compaction counts their digits)
-    pair_scan = 2 + 1 + 1             # block sums, scan of partials, pair offsets, emission
+    pair_scan = 1 + 1                 # one-pass pair offsets (look-back), emission
     tile_sort = tile_passes           # one-sweep passes (the emission counts their digits)
     binning = compaction + depth_sort + pair_scan + tile_sort + 1 + 1   # ranges, work order
     # render fwd; backward clear of the visible 2D-gradient rows, composite bwd, preprocess bwd

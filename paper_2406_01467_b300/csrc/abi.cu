@@ -167,8 +167,6 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   for (int i = 0; i < 2; ++i) { L.vkey[i] = take(4 * (size_t)E); L.vval[i] = take(4 * (size_t)E); }
   L.pair_off = take(4 * (size_t)E);
   L.chunk_first = take(4 * (size_t)((L.Pcap + kEmitChunk - 1) / kEmitChunk + 1));
-  const int nbmax = std::max(L.nb_E, L.nb_P);
-  L.blk = take(4 * (size_t)nbmax);
   for (int i = 0; i < 2; ++i) { L.ptile[i] = take(4 * (size_t)L.Pcap); L.pval[i] = take(4 * (size_t)L.Pcap); }
   const int passes = (tile_sort_bits(T) + kRadixBits - 1) / kRadixBits;
   L.ptile_final = L.ptile[passes & 1];
@@ -176,8 +174,9 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   // histograms + tickets, then the look-back words of the 4 depth passes or of the tile passes
   L.sortaux_bytes[0] = 8192 + (size_t)4 * L.nb_E * kRadix * 8;
   L.sortaux_bytes[1] = 8192 + (size_t)passes * L.nb_P * kRadix * 8;
-  L.sortaux[0] = take(L.sortaux_bytes[0]);   // these three regions are contiguous:
+  L.sortaux[0] = take(L.sortaux_bytes[0]);   // these four regions are contiguous:
   L.sortaux[1] = take(L.sortaux_bytes[1]);   // binning clears them with one memset
+  L.scanaux = take(64 + 2 * 8 * (size_t)L.nb_E);
   L.ranges = take(8 * (size_t)T);
   L.tile_order = take(4 * (size_t)T);
   const bool bwd_state = !p.geometry_only;   // per-pixel replay state and 2D gradients

@@ -85,73 +85,6 @@ __device__ inline uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, ui
   return r;
 }
 
-// ---------------------------------------------------------------------------
-// Generic per-block partial sums and the scan of those partials
-// ---------------------------------------------------------------------------
-// mode 0: count entries with a valid depth key (items = entries)
-// mode 1: sum tiles_touched over depth-sorted entries (items = visible entries)
-template <int MODE>
-__global__ void __launch_bounds__(kSortThreads)
-k_block_sums(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
-             const unsigned long long* count_ptr, int64_t n_fixed, uint32_t* blk) {
-  __shared__ uint32_t s_warp[33];
-  const int64_t n = count_ptr ? clamp_count(count_ptr, n_fixed) : n_fixed;
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  uint32_t sum = 0;
-  for (int r = 0; r < kSortItems; ++r) {
-    int64_t i = base + r * kSortThreads + threadIdx.x;
-    if (i < n) {
-      if (MODE == 0) sum += a[i] != kInvalidKey ? 1u : 0u;
-      else sum += a[b[i]];
-    }
-  }
-  uint32_t tot;
-  block_exclusive_scan(sum, s_warp, &tot);
-  if (threadIdx.x == 0) blk[blockIdx.x] = tot;
-}
-
-// One block: exclusive scan of nb partials in place; the grand total goes to
-// *total_out.  If cap > 0 and the total exceeds it, the capacity error is set.
-__global__ void __launch_bounds__(1024)
-k_scan_partials(uint32_t* blk, int nb, unsigned long long* total_out, int64_t cap, Header* hdr) {
-  __shared__ uint32_t s_warp[33];
-  __shared__ unsigned long long s_run;
-  if (threadIdx.x == 0) s_run = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int base = 0; base < nb; base += 1024) {
-    int i = base + threadIdx.x;
-    uint32_t v = i < nb ? blk[i] : 0u;
-    uint32_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(FULL, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[w] = x;
-    __syncthreads();
-    if (w == 0) {
-      uint32_t t = s_warp[lane];
-      uint32_t s = t;
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(FULL, s, o);
-        if (lane >= o) s += y;
-      }
-      s_warp[lane] = s - t;
-      if (lane == 31) s_warp[32] = s;
-    }
-    __syncthreads();
-    unsigned long long run = s_run;
-    if (i < nb) blk[i] = (uint32_t)(run + (x - v) + s_warp[w]);
-    __syncthreads();
-    if (threadIdx.x == 0) s_run = run + s_warp[32];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    *total_out = s_run;
-    if (cap > 0 && s_run > (unsigned long long)cap) set_status(hdr, GS_ERR_CAPACITY);
-  }
-}
-
 // In-block ordered scan helper: each warp owns 512 consecutive items
 // (16 rounds of 32), so item order = (warp, round, lane).
 struct WarpItems {
@@ -161,15 +94,90 @@ struct WarpItems {
   }
 };
 
-// Compaction of visible entries: (key, entry) at their rank among visible ones.
+// ---------------------------------------------------------------------------
+// Decoupled look-back.  A block publishes one 64-bit word per value: its own
+// total flagged A as soon as it is known, then the inclusive prefix flagged P;
+// a successor adds A words going back until it meets a P.  Blocks take their
+// index from a ticket counter in the order they start, so a block only ever
+// waits for blocks that are already running; every wait is bounded and sets
+// GS_ERR_TIMEOUT if it runs out.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62, kFlagMask = 3ull << 62;
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ inline void st_relaxed(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ inline unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// The block's ticket (thread 0 draws it; every thread gets it).
+__device__ inline int block_ticket(int* ticket, int* s_tk) {
+  if (threadIdx.x == 0) *s_tk = atomicAdd(ticket, 1);
+  __syncthreads();
+  return *s_tk;
+}
+
+// Exclusive prefix over the blocks before blk of their totals (agg: this
+// block's total, as seen by warp 0).  Called by every thread of the block;
+// warp 0 reads the words of 32 predecessors at a time (lane l: block j - l)
+// and adds them up to the nearest P.
+__device__ inline unsigned long long block_lookback(unsigned long long* words, int blk, unsigned long long agg,
+                                                    Header* hdr, unsigned long long* s_excl) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    unsigned long long* mine = words + blk;
+    if (lane == 0) st_relaxed(mine, (blk == 0 ? kFlagP : kFlagA) | agg);
+    unsigned long long excl = 0;
+    int j = blk - 1, spins = 0;
+    while (j >= 0) {
+      const int q = j - lane;
+      // before block 0: a zero inclusive prefix (never consumed: block 0 always publishes P)
+      const unsigned long long f = q >= 0 ? ld_relaxed(words + q) : kFlagP;
+      const unsigned long long st = f & kFlagMask;
+      const unsigned pm = __ballot_sync(FULL, st == kFlagP), zm = __ballot_sync(FULL, st == 0);
+      const int last = pm ? __ffs(pm) - 1 : 31;                  // lanes 0..last are needed
+      const unsigned need = last == 31 ? FULL : (2u << last) - 1u;
+      if (zm & need) {                                           // one of them is not published yet
+        if (++spins > kSpinLimit) {
+          if (lane == 0) set_status(hdr, GS_ERR_TIMEOUT);
+          break;
+        }
+        continue;
+      }
+      unsigned long long c = lane <= last ? (f & ~kFlagMask) : 0ull;
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+      excl += c;
+      if (pm) break;
+      j -= 32;
+    }
+    if (lane == 0) {
+      if (blk > 0) st_relaxed(mine, kFlagP | (excl + agg));
+      *s_excl = excl;
+    }
+  }
+  __syncthreads();
+  return *s_excl;
+}
+
+// Compaction of visible entries: (key, entry) at their rank among visible
+// ones, in one pass (block offsets by look-back); the last block writes the
+// visible count.  Also counts the depth keys' digits for the sort.
 __global__ void __launch_bounds__(kSortThreads)
-k_compact(const uint32_t* __restrict__ key, int64_t E, const uint32_t* __restrict__ blk,
-          uint32_t* __restrict__ okey, uint32_t* __restrict__ oval, uint32_t* __restrict__ ghist) {
+k_compact(const uint32_t* __restrict__ key, int64_t E, uint32_t* __restrict__ okey, uint32_t* __restrict__ oval,
+          uint32_t* __restrict__ ghist, unsigned long long* __restrict__ words, int* ticket,
+          unsigned long long* __restrict__ n_vis_out, Header* hdr) {
   __shared__ uint32_t s_wtot[8];
   __shared__ uint32_t s_h[kMaxPasses][kRadix];   // the depth sort's digit histograms
+  __shared__ int s_tk;
+  __shared__ unsigned long long s_excl;
   for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
+  const int blk = block_ticket(ticket, &s_tk);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const int64_t base = (int64_t)blk * kSortTile;
   uint32_t k[kSortItems];
   uint32_t wsum = 0;
   for (int r = 0; r < kSortItems; ++r) {
@@ -179,8 +187,14 @@ k_compact(const uint32_t* __restrict__ key, int64_t E, const uint32_t* __restric
   }
   if (lane == 0) s_wtot[w] = wsum;
   __syncthreads();
-  uint32_t off = blk[blockIdx.x];
-  for (int i = 0; i < w; ++i) off += s_wtot[i];
+  uint32_t tot = 0, before = 0;
+  for (int i = 0; i < 8; ++i) {
+    before += i < w ? s_wtot[i] : 0u;
+    tot += s_wtot[i];
+  }
+  const unsigned long long excl = block_lookback(words, blk, tot, hdr, &s_excl);
+  if (threadIdx.x == 0 && base + kSortTile >= E) *n_vis_out = excl + tot;   // the last block
+  uint32_t off = (uint32_t)excl + before;
   for (int r = 0; r < kSortItems; ++r) {
     const bool v = k[r] != kInvalidKey;
     const unsigned bal = __ballot_sync(FULL, v);
@@ -195,17 +209,25 @@ k_compact(const uint32_t* __restrict__ key, int64_t E, const uint32_t* __restric
   hist_flush(s_h, kMaxPasses, ghist);
 }
 
-// Global exclusive scan of tiles_touched in depth order: pair_off[k] is the
-// first pair of the k-th nearest visible entry.
+// Exclusive scan of tiles_touched in depth order, in one pass: pair_off[k] is
+// the first pair of the k-th nearest visible entry.  The block holding the
+// last entry writes the pair count and checks it against the capacity.
 __global__ void __launch_bounds__(kSortThreads)
 k_pair_offsets(const uint32_t* __restrict__ sval, const unsigned long long* n_vis_ptr, int64_t E,
-               const uint32_t* __restrict__ touched, const uint32_t* __restrict__ blk,
-               uint32_t* __restrict__ pair_off, uint32_t* __restrict__ chunk_first, int64_t n_chunks) {
+               const uint32_t* __restrict__ touched, uint32_t* __restrict__ pair_off,
+               uint32_t* __restrict__ chunk_first, int64_t n_chunks, unsigned long long* __restrict__ words,
+               int* ticket, unsigned long long* __restrict__ n_pairs_out, int64_t cap, Header* hdr) {
   __shared__ uint32_t s_wtot[8];
+  __shared__ int s_tk;
+  __shared__ unsigned long long s_excl;
+  const int blk = block_ticket(ticket, &s_tk);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t n = clamp_count(n_vis_ptr, E);
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  if (base >= n) return;
+  const int64_t base = (int64_t)blk * kSortTile;
+  if (base >= n) {   // so do all later tickets: nobody waits for this block
+    if (blk == 0 && threadIdx.x == 0) *n_pairs_out = 0;   // no visible entry
+    return;
+  }
   uint32_t cnt[kSortItems];
   uint32_t wsum = 0;
 #pragma unroll
@@ -221,8 +243,17 @@ k_pair_offsets(const uint32_t* __restrict__ sval, const unsigned long long* n_vi
   }
   if (lane == 0) s_wtot[w] = wsum;
   __syncthreads();
-  uint32_t off = blk[blockIdx.x];
-  for (int i = 0; i < w; ++i) off += s_wtot[i];
+  uint32_t tot = 0, before = 0;
+  for (int i = 0; i < 8; ++i) {
+    before += i < w ? s_wtot[i] : 0u;
+    tot += s_wtot[i];
+  }
+  const unsigned long long excl = block_lookback(words, blk, tot, hdr, &s_excl);
+  if (threadIdx.x == 0 && base + kSortTile >= n) {   // the block holding the last entry
+    *n_pairs_out = excl + tot;
+    if (cap > 0 && excl + tot > (unsigned long long)cap) set_status(hdr, GS_ERR_CAPACITY);
+  }
+  uint32_t off = (uint32_t)excl + before;
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     uint32_t x = cnt[r];
@@ -420,17 +451,6 @@ cudaError_t launch_tile_order(void* ws, const Layout& L, const uint32_t* cost, i
 // counter), so a block only ever waits for blocks that are already running;
 // every wait is bounded and sets GS_ERR_TIMEOUT if it runs out.
 // ---------------------------------------------------------------------------
-constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62, kFlagMask = 3ull << 62;
-constexpr int kSpinLimit = 1 << 22;
-
-__device__ inline void st_relaxed(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ inline unsigned long long ld_relaxed(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
 
 __global__ void __launch_bounds__(kSortThreads, 3)
 k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
@@ -566,33 +586,32 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   Header* hdr = at<Header>(ws, L.hdr);
   uint32_t* key = at<uint32_t>(ws, L.key);
   uint32_t* touched = at<uint32_t>(ws, L.touched);
-  uint32_t* blk = at<uint32_t>(ws, L.blk);
+  int* scan_ticket = at<int>(ws, L.scanaux);   // [0]: compaction, [1]: pair offsets
+  unsigned long long* scan_words = at<unsigned long long>(ws, L.scanaux + 64);   // [2][nb_E]
   uint32_t *vk0 = at<uint32_t>(ws, L.vkey[0]), *vk1 = at<uint32_t>(ws, L.vkey[1]);
   uint32_t *vv0 = at<uint32_t>(ws, L.vval[0]), *vv1 = at<uint32_t>(ws, L.vval[1]);
   uint32_t *pt0 = at<uint32_t>(ws, L.ptile[0]), *pt1 = at<uint32_t>(ws, L.ptile[1]);
   uint32_t *pv0 = at<uint32_t>(ws, L.pval[0]), *pv1 = at<uint32_t>(ws, L.pval[1]);
   (void)hf;
-  // 0. one memset clears both sorts' auxiliary words and the tile ranges (contiguous)
+  // 0. one memset clears both sorts' and both scans' auxiliary words and the
+  //    tile ranges (contiguous)
   cudaError_t e0 = cudaMemsetAsync(at<char>(ws, L.sortaux[0]), 0, L.ranges + 8 * (size_t)L.T - L.sortaux[0], s);
   if (e0 != cudaSuccess) return e0;
-  // 1. compaction
-  k_block_sums<0><<<L.nb_E, kSortThreads, 0, s>>>(key, nullptr, nullptr, L.E, blk);
-  k_scan_partials<<<1, 1024, 0, s>>>(blk, L.nb_E, &hdr->n_vis, 0, hdr);
-  // (the compaction also counts the depth keys' digits for the sort)
-  k_compact<<<L.nb_E, kSortThreads, 0, s>>>(key, L.E, blk, vk0, vv0, at<uint32_t>(ws, L.sortaux[0]));
+  // 1. compaction (also counts the depth keys' digits for the sort)
+  k_compact<<<L.nb_E, kSortThreads, 0, s>>>(key, L.E, vk0, vv0, at<uint32_t>(ws, L.sortaux[0]), scan_words,
+                                           scan_ticket, &hdr->n_vis, hdr);
   // 2. depth sort: 31 bits (z > 0, so the sign bit is clear)
   cudaError_t err = radix_sort(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, at<void>(ws, L.sortaux[0]),
                                L.sortaux_bytes[0], hdr, s);
   if (err != cudaSuccess) return err;
-  // 3. pair offsets
-  k_block_sums<1><<<L.nb_E, kSortThreads, 0, s>>>(touched, vv0, &hdr->n_vis, L.E, blk);
-  k_scan_partials<<<1, 1024, 0, s>>>(blk, L.nb_E, &hdr->n_pairs, L.Pcap, hdr);
-  // 4. emission
+  // 3. pair offsets (the pair count and the capacity check)
   uint32_t* pair_off = at<uint32_t>(ws, L.pair_off);
   uint32_t* chunk_first = at<uint32_t>(ws, L.chunk_first);
   const int64_t n_chunks = (L.Pcap + kEmitChunk - 1) / kEmitChunk + 1;
-  k_pair_offsets<<<L.nb_E, kSortThreads, 0, s>>>(vv0, &hdr->n_vis, L.E, touched, blk, pair_off, chunk_first,
-                                                  n_chunks);
+  k_pair_offsets<<<L.nb_E, kSortThreads, 0, s>>>(vv0, &hdr->n_vis, L.E, touched, pair_off, chunk_first, n_chunks,
+                                                  scan_words + L.nb_E, scan_ticket + 1, &hdr->n_pairs, L.Pcap,
+                                                  hdr);
+  // 4. emission
   // (the emission also counts the tile keys' digits for the sort)
   const int bits = tile_sort_bits(L.T);
   const int tile_passes = (bits + kRadixBits - 1) / kRadixBits;

@@ -140,11 +140,11 @@ struct Layout {
   size_t vkey[2], vval[2];  // depth sort ping-pong
   size_t pair_off;          // exclusive scan of tiles_touched in depth order
   size_t chunk_first;       // [Pcap / kEmitChunk + 1] entry holding each emission chunk's first pair
-  size_t blk;               // per-block partials of the scans
+  size_t scanaux;           // the two scans: tickets (64 B), then nb_E look-back words each
   size_t ptile[2], pval[2]; // pair sort ping-pong
   size_t ptile_final, pval_final;  // where the sorted pairs end up
   size_t sortaux[2];        // depth and tile radix sorts: digit histograms, tickets, look-back
-  size_t sortaux_bytes[2];  // words; both and the tile ranges are cleared by one memset
+  size_t sortaux_bytes[2];  // words; they, the scan words and the tile ranges are cleared by one memset
   size_t ranges;            // [T] int2
   size_t tile_order;        // [T] int: compositing work order (heaviest tiles first)
   size_t px_T, px_last, px_med;
