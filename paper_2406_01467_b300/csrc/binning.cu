@@ -394,11 +394,27 @@ __global__ void __launch_bounds__(256)
 k_ranges(const uint32_t* __restrict__ ptile, const unsigned long long* n_pairs_ptr, int64_t cap,
          int2* __restrict__ ranges) {
   const int64_t P = clamp_count(n_pairs_ptr, cap);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t t = ptile[i];
-    if (i == 0 || ptile[i - 1] != t) ranges[t].x = (int)i;
-    if (i == P - 1 || ptile[i + 1] != t) ranges[t].y = (int)(i + 1);
+  // four consecutive pairs per thread: one 16-byte load (the buffer is 16-byte
+  // aligned), scalar loads for its two neighbours and for a ragged tail
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; 4 * q < P;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = 4 * q;
+    uint32_t t[6];
+    if (i0 + 4 <= P) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(ptile) + q);
+      t[1] = v.x; t[2] = v.y; t[3] = v.z; t[4] = v.w;
+    } else {
+      for (int k = 0; k < 4; ++k) t[1 + k] = i0 + k < P ? ptile[i0 + k] : 0xFFFFFFFFu;
+    }
+    t[0] = i0 > 0 ? ptile[i0 - 1] : 0xFFFFFFFFu;
+    t[5] = i0 + 4 < P ? ptile[i0 + 4] : 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = i0 + k;
+      if (i >= P) break;
+      if (i == 0 || t[k] != t[k + 1]) ranges[t[k + 1]].x = (int)i;
+      if (i == P - 1 || t[k + 2] != t[k + 1]) ranges[t[k + 1]].y = (int)(i + 1);
+    }
   }
 }
 
@@ -625,7 +641,7 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   if (err != cudaSuccess) return err;
   uint32_t* ptile = at<uint32_t>(ws, L.ptile_final);
   // 6. ranges
-  int g = (int)std::min<int64_t>((L.Pcap + 255) / 256, 148 * 32);
+  int g = (int)std::max<int64_t>(1, std::min<int64_t>((L.Pcap / 4 + 255) / 256, 148 * 16));
   k_ranges<<<g, 256, 0, s>>>(ptile, &hdr->n_pairs, L.Pcap, at<int2>(ws, L.ranges));
   // 7. compositing work order (by list length)
   return launch_tile_order(ws, L, nullptr, at<int>(ws, L.tile_order), s);
