@@ -283,9 +283,8 @@ gs_status gs_adam_step(float* params, float* grads, float* m, float* v, int64_t 
 
 /* Intermediate results for tests and tools, copied to caller device buffers on
  * `stream`; any pointer may be NULL.  rec: [n_entries][16] FP32 per-entry
- * records (u, v, conic a b c, opacity, sigma cut, z, p0 p1, n1 n2, r g b, n0);
- * (the sigma cut is ln(o / alpha_min) plus a margin: beyond it a splat cannot
- * reach alpha_min); rect: [n_entries][4] int32 pixel rectangle (i0, i1, j0, j1), (0,-1,0,-1)
+ * records (u, v, conic a b c, opacity, n1 n2, p0 p1, z, 0, r g b, n0);
+ * rect: [n_entries][4] int32 pixel rectangle (i0, i1, j0, j1), (0,-1,0,-1)
  * when culled; pair_tile/pair_entry: [pair_capacity] int32 sorted pairs;
  * ranges: [total tiles][2] int32.  grad2d: [n_entries][16] FP32 per-entry sums
  * of the compositing backward, valid after gs_render_bwd: with gs = dL/dsigma

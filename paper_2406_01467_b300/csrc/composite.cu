@@ -128,9 +128,13 @@ __device__ inline SubRect sub_rect(int x0, int y0, int sub_per_row, int sub) {
 }
 
 // Can the splat (first two record float4s) reach any pixel of the rectangle?
-__device__ inline bool reaches(const float4& f0, const float4& f1, const SubRect& R) {
+// sigma_cut: beyond it alpha < alpha_min, with a margin (1e-4 relative and
+// absolute) far above the error of the FP32 operations and of __logf, so the
+// test only ever skips splats the alpha test rejects at every pixel.
+__device__ inline bool reaches(const float4& f0, const float4& f1, const SubRect& R, float amin) {
   const float ia = __fdividef(1.f, f0.z), ic = __fdividef(1.f, f1.x);
-  return rect_min_sigma(f0.x, f0.y, f0.z, f0.w, f1.x, ia, ic, R.X0, R.X1, R.Y0, R.Y1) <= f1.z;
+  const float cut = __logf(__fdividef(f1.y, amin)) * 1.0001f + 1e-4f;
+  return rect_min_sigma(f0.x, f0.y, f0.z, f0.w, f1.x, ia, ic, R.X0, R.X1, R.Y0, R.Y1) <= cut;
 }
 
 // Asynchronous global->shared copies (cp.async): each lane stages whole
@@ -195,7 +199,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
     cp_async_wait<1>();     // this lane's copies of chunk c0 have landed
     __syncwarp();           // ... and every lane's are visible
     float4 (*my)[32] = buf[cur];
-    const bool rel = c0 + lane < range.y && reaches(my[0][lane], my[1][lane], R);
+    const bool rel = c0 + lane < range.y && reaches(my[0][lane], my[1][lane], R, amin);
     unsigned m = __ballot_sync(kFull, rel);
     uint32_t cm = 0;        // records of the chunk this lane blends
     while (m) {
@@ -214,8 +218,8 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float w = al * T;
       const float4 e2 = my[2][j], e3 = my[3][j];
       if (!GEO) { C0 += w * e3.x; C1 += w * e3.y; C2 += w * e3.z; }
-      N0 += w * e3.w; N1 += w * e2.z; N2 += w * e2.w;
-      const float dk = b.w + e2.x * dx + e2.y * dy;   // Eq. 4
+      N0 += w * e3.w; N1 += w * b.z; N2 += w * b.w;
+      const float dk = e2.z + e2.x * dx + e2.y * dy;   // Eq. 4
       if (LOSS) {
         if (last < 0) d0 = dk;
         const float sd = dk - d0;
@@ -245,8 +249,8 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   if (med < 0 && last >= 0) {   // median never reached: depth of the last contributor
     med = last;
     const float4* r = rec + 4 * (int64_t)pval[last];
-    const float4 a = r[0], b = r[1], e2 = r[2];
-    depth = b.w + e2.x * (a.x - fpx) + e2.y * (a.y - fpy);
+    const float4 a = r[0], e2 = r[2];
+    depth = e2.z + e2.x * (a.x - fpx) + e2.y * (a.y - fpy);
   }
   const int64_t HW = (int64_t)c.W * c.H;
   const int64_t p = c.pix_local;
@@ -385,7 +389,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float4* r = rec + 4 * (int64_t)e;
       my[0][lane] = __ldg(r);
       my[1][lane] = __ldg(r + 1);
-      my[2][lane] = __ldg(r + 2);
+      if (LOSS) my[2][lane] = __ldg(r + 2);
       my[3][lane] = __ldg(r + 3);
       my_e[lane] = e;
     }
@@ -404,7 +408,9 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       // backward applies the constants once per entry
       float2 gr[8];
       const bool live = idx <= last;
-      const float4 a = my[0][j], b = my[1][j], e2 = my[2][j], e3 = my[3][j];
+      // the depth plane (p, z) only for Eq. 23
+      const float4 a = my[0][j], b = my[1][j], e3 = my[3][j];
+      const float4 e2 = LOSS ? my[2][j] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float2 d = __fadd2_rn(make_float2(a.x, a.y), nfp);     // (dx, dy)
       const float dx = d.x, dy = d.y;
       const float2 d2 = __fmul2_rn(d, d);                           // (dx^2, dy^2)
@@ -419,7 +425,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float w = al * T;
       const float2 w2 = make_float2(w, w);
       // colour and normal: (rgb, n) and the upstream (dC, dN) as three pairs
-      const float2 x0 = make_float2(e3.x, e3.y), x1 = make_float2(e3.z, e3.w), x2 = make_float2(e2.z, e2.w);
+      const float2 x0 = make_float2(e3.x, e3.y), x1 = make_float2(e3.z, e3.w), x2 = make_float2(b.z, b.w);
       gr[5] = __fmul2_rn(w2, U45);
       gr[6] = __fmul2_rn(w2, U01);
       gr[7] = __fmul2_rn(w2, U23);
@@ -437,7 +443,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float dal = contrib ? T * (acc.x + acc.y) + dATf * ia : 0.f;
       // d = z_c + p . Delta (Eq. 4): the median splat, and Eq. 23 with the weights constant
       float sd = (contrib && idx == med) ? dD : 0.f;
-      if (LOSS) sd += c4 * w * ((b.w + e2.x * dx + e2.y * dy) - dmean);
+      if (LOSS) sd += c4 * w * ((e2.z + e2.x * dx + e2.y * dy) - dmean);
       gr[3] = make_float2(0.f, sd);
       gr[4] = __fmul2_rn(make_float2(sd, sd), d);
       // alpha = o G below the clamp: dL/dsigma = -dL/dalpha alpha
@@ -471,7 +477,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float s = reduce_rows(my_red);   // lanes 16-31 read stale rows without jB
       __syncwarp();   // the scratch is rewritten by the next round
       const int slot = lane & 15, j = lane < 16 ? jA : jB;
-      if (j >= 0 && slot != R_CUT && s != 0.f) atomicAdd(grad + (int64_t)my_e[j] * kRecFloats + slot, s);
+      if (j >= 0 && slot != G_UNUSED && s != 0.f) atomicAdd(grad + (int64_t)my_e[j] * kRecFloats + slot, s);
     }
     __syncwarp();
   }

@@ -19,13 +19,18 @@ constexpr int kRadixBits = 8;
 constexpr int kEmitChunk = 2048;          // pairs per emission slice
 constexpr int kRadix = 1 << kRadixBits;
 
-// Record slots (one 64-byte record per (view, Gaussian) entry).
-// The first two float4s hold everything the alpha test needs.
-enum RecSlot {
-  R_U = 0, R_V = 1, R_CA = 2, R_CB = 3,      // float4 #0: centre, conic a b
-  R_CC = 4, R_O = 5, R_CUT = 6, R_Z = 7,     // float4 #1: conic c, opacity, sigma cut, z_c
-  R_P0 = 8, R_P1 = 9, R_N1 = 10, R_N2 = 11,  // float4 #2: depth plane p, normal y z
-  R_R = 12, R_G = 13, R_B = 14, R_N0 = 15    // float4 #3: colour, normal x
+// The record of a (view, Gaussian) entry: four float4s
+//   #0 (u, v, conic a, conic b)   #1 (conic c, opacity, n_y, n_z)
+//   #2 (p0, p1, z_c, 0)           #3 (r, g, b, n_x)
+// #0 and #1 hold everything the alpha test needs; #2 only the planar depth.
+// Slots of the per-entry 2D-gradient row the compositing backward accumulates
+// (gs = dL/dsigma, sd = dL/dd per pixel; the preprocess backward turns the
+// first ten into record gradients with the entry's conic, p and opacity):
+enum GradSlot {
+  G_U = 0, G_V = 1, G_CA = 2, G_CB = 3,      // S gs dx, S gs dy, S gs dx^2, S gs dx dy
+  G_CC = 4, G_O = 5, G_UNUSED = 6, G_Z = 7,  // S gs dy^2, S gs, -, S sd
+  G_P0 = 8, G_P1 = 9, G_N1 = 10, G_N2 = 11,  // S sd dx, S sd dy, dL/dn_y, dL/dn_z
+  G_R = 12, G_G = 13, G_B = 14, G_N0 = 15    // dL/d(r, g, b), dL/dn_x
 };
 
 struct ViewDev {

@@ -427,12 +427,9 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
     }
     if (valid) {
       float4* r = rec + 4 * e;
-      // sigma beyond which alpha < alpha_min (with a margin far above FP32 error):
-      // lets the compositing skip a splat for a whole block of pixels
-      const float cut = logf(o / amin) * 1.0001f + 1e-4f;
       r[0] = make_float4(u, v, conic[0], conic[1]);
-      r[1] = make_float4(conic[2], o, cut, z);
-      r[2] = make_float4(pp[0], pp[1], nn[1], nn[2]);
+      r[1] = make_float4(conic[2], o, nn[1], nn[2]);
+      r[2] = make_float4(pp[0], pp[1], z, 0.f);
       r[3] = make_float4(rgb[0], rgb[1], rgb[2], nn[0]);
       rect[e] = make_short4((short)i0, (short)i1, (short)j0, (short)j1);
       key[e] = __float_as_uint(z);

@@ -60,13 +60,11 @@ def test_records_match_oracle_tiny():
         scale = np.abs(pre["conic"][v]).max(axis=1)
         np.testing.assert_array_less(np.abs(rec[v, col] - pre["conic"][v, k]), 1e-4 * scale + 1e-9)
     np.testing.assert_allclose(rec[v, 5], pre["opacity"][v], rtol=1e-7)
-    np.testing.assert_allclose(rec[v, 7], pre["z"][v], rtol=1e-6)
+    np.testing.assert_allclose(rec[v, 10], pre["z"][v], rtol=1e-6)
     np.testing.assert_allclose(rec[v, 8:10], pre["p"][v], atol=1e-5)
-    np.testing.assert_allclose(rec[v][:, [15, 10, 11]], pre["n"][v], atol=1e-5)   # (n_x | p, n_y, n_z)
+    np.testing.assert_allclose(rec[v][:, [15, 6, 7]], pre["n"][v], atol=1e-5)   # (n_x | n_y, n_z)
     np.testing.assert_allclose(rec[v, 12:15], pre["rgb"][v], atol=1e-5)
-    # the sigma cut bounds the alpha test: exp(-cut) * o <= alpha_min
-    cut = rec[v, 6]
-    assert (pre["opacity"][v] * np.exp(-cut.astype(np.float64)) <= np.float32(p.alpha_min)).all()
+    assert (rec[v, 11] == 0).all()
 
 
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 8)])
