@@ -472,7 +472,9 @@ __global__ void __launch_bounds__(kSortThreads, 3)
 k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
            uint32_t* __restrict__ vout, const unsigned long long* count_ptr, int64_t cap, int pass,
            const uint32_t* __restrict__ ghist, unsigned long long* __restrict__ look, int* ticket, Header* hdr) {
-  __shared__ uint32_t s_wcnt[8][kRadix];   // [warp][digit]: per-lane digit accesses spread over the banks
+  // [half][warp][digit] running digit counts of a warp's two halves of items
+  // (rounds 0-7 and 8-15: two independent chains), then [0]: the warps' bases
+  __shared__ uint16_t s_wc[2][8][kRadix];
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
   __shared__ uint32_t s_dstart[kRadix];
@@ -482,7 +484,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   const int w = threadIdx.x >> 5;
   const int shift = kRadixBits * pass;
   if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1);
-  for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) reinterpret_cast<uint32_t*>(&s_wc[0][0][0])[i] = 0;
   __syncthreads();
   const int blk = s_blk;
   const int64_t n = clamp_count(count_ptr, cap);
@@ -502,27 +504,40 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
     v[r] = li < nloc ? __ldg(vb + li) : 0u;
   }
   // the peer masks of all items first (independent of one another), then the
-  // warp's running digit counts item by item
+  // warp's running digit counts item by item, rounds r and r + 8 side by side
+  // in two counter sets
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const int d = li0 + 32 * r < nloc ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
     // a digit shared by the whole warp needs no matching
     rank[r] = __all_sync(FULL, d == __shfl_sync(FULL, d, 0)) ? FULL : __match_any_sync(FULL, d);
   }
+  constexpr int kHalf = kSortItems / 2;
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
+  for (int r = 0; r < kHalf; ++r) {
+    const int r2 = r + kHalf;
+    const int dA = li0 + 32 * r < nloc ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
+    const int dB = li0 + 32 * r2 < nloc ? (int)((k[r2] >> shift) & (kRadix - 1)) : kRadix;
+    const unsigned pA = rank[r], pB = rank[r2];
+    const uint32_t oA = dA < kRadix ? s_wc[0][w][dA] : 0u;
+    const uint32_t oB = dB < kRadix ? s_wc[1][w][dB] : 0u;
+    rank[r] = oA + __popc(pA & lt);
+    rank[r2] = oB + __popc(pB & lt);
+    __syncwarp();
+    if (dA < kRadix && (pA & lt) == 0) s_wc[0][w][dA] = (uint16_t)(oA + __popc(pA));
+    if (dB < kRadix && (pB & lt) == 0) s_wc[1][w][dB] = (uint16_t)(oB + __popc(pB));
+    __syncwarp();
+  }
+  // the second half's items follow the first half's items of the same digit
+#pragma unroll
+  for (int r = kHalf; r < kSortItems; ++r) {
     const int d = li0 + 32 * r < nloc ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
-    const unsigned peers = rank[r];
-    const uint32_t old = d < kRadix ? s_wcnt[w][d] : 0u;
-    rank[r] = old + __popc(peers & lt);
-    __syncwarp();
-    if (d < kRadix && (peers & lt) == 0) s_wcnt[w][d] = old + __popc(peers);
-    __syncwarp();
+    if (d < kRadix) rank[r] += s_wc[0][w][d];
   }
   __syncthreads();
   const int d = threadIdx.x;   // one thread per digit from here on
   uint32_t c[8], cnt = 0;
-  for (int i = 0; i < 8; ++i) { c[i] = s_wcnt[i][d]; cnt += c[i]; }
+  for (int i = 0; i < 8; ++i) { c[i] = (uint32_t)s_wc[0][i][d] + s_wc[1][i][d]; cnt += c[i]; }
   unsigned long long* mine = look + (int64_t)blk * kRadix + d;
   st_relaxed(mine, (blk == 0 ? kFlagP : kFlagA) | cnt);   // successors may start looking
   // block-local exclusive scan over (digit, warp) in digit-major order, and the
@@ -531,7 +546,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   const uint32_t dbase = block_exclusive_scan(ghist[pass * kRadix + d], s_warp, nullptr);
   s_dstart[d] = start;
   uint32_t run = start;
-  for (int i = 0; i < 8; ++i) { s_wcnt[i][d] = run; run += c[i]; }
+  for (int i = 0; i < 8; ++i) { s_wc[0][i][d] = (uint16_t)run; run += c[i]; }   // bases <= 4096
   // decoupled look-back: keys of digit d in the blocks before this one
   uint32_t excl = 0;
   if (blk > 0) {
@@ -554,7 +569,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   for (int r = 0; r < kSortItems; ++r) {
     if (li0 + 32 * r < nloc) {
       const int dd = (int)((k[r] >> shift) & (kRadix - 1));
-      const uint32_t pos = s_wcnt[w][dd] + rank[r];
+      const uint32_t pos = s_wc[0][w][dd] + rank[r];
       s_keys[pos] = k[r];
       s_vals[pos] = v[r];
     }
