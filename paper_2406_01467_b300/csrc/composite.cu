@@ -179,7 +179,9 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
 
   // per-chunk masks of blended records of this 8x4 block (word k: chunk k of the list)
   uint32_t* cmask = at<uint32_t>(ws, L.cmask) + (int64_t)sub * L.cmask_words + (range.x >> 5) + tile;
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, depth = 0.f;
+  float T = 1.f, depth = 0.f;
+  // blended (r, g), (b, n0), (n1, n2): the record's aligned pairs
+  float2 Crg = make_float2(0.f, 0.f), Cbn = make_float2(0.f, 0.f), N12 = make_float2(0.f, 0.f);
   float Ws = 0.f, S1 = 0.f, S2 = 0.f, d0 = 0.f;   // Eq. 23 moments (LOSS only)
   int last = -1, med = -1;
   uint32_t nblend = 0;
@@ -217,8 +219,10 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       cm |= 1u << j;
       const float w = al * T;
       const float4 e2 = my[2][j], e3 = my[3][j];
-      if (!GEO) { C0 += w * e3.x; C1 += w * e3.y; C2 += w * e3.z; }
-      N0 += w * e3.w; N1 += w * b.z; N2 += w * b.w;
+      const float2 w2 = make_float2(w, w);
+      if (!GEO) Crg = __ffma2_rn(w2, make_float2(e3.x, e3.y), Crg);
+      Cbn = __ffma2_rn(w2, make_float2(e3.z, e3.w), Cbn);   // (b, n0); b is 0 in GEO records
+      N12 = __ffma2_rn(w2, make_float2(b.z, b.w), N12);
       const float dk = e2.z + e2.x * dx + e2.y * dy;   // Eq. 4
       if (LOSS) {
         if (last < 0) d0 = dk;
@@ -256,11 +260,11 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   const int64_t p = c.pix_local;
   if (!GEO && maps.color) {
     float* col = maps.color + 3 * c.pix_base;
-    col[p] = C0; col[HW + p] = C1; col[2 * HW + p] = C2;
+    col[p] = Crg.x; col[HW + p] = Crg.y; col[2 * HW + p] = Cbn.x;
   }
   if (maps.normal) {
     float* nrm = maps.normal + 3 * c.pix_base;
-    nrm[p] = N0; nrm[HW + p] = N1; nrm[2 * HW + p] = N2;
+    nrm[p] = Cbn.y; nrm[HW + p] = N12.x; nrm[2 * HW + p] = N12.y;
   }
   if (maps.alpha) maps.alpha[c.pix] = 1.f - T;
   if (maps.depth) maps.depth[c.pix] = depth;
@@ -274,9 +278,9 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
     const int64_t NP = L.NPIX;
     P[LP_MEAN * NP + c.pix] = Ws > 0.f ? d0 + S1 / Ws : 0.f;
     P[LP_DEPTH * NP + c.pix] = depth;
-    P[LP_N0 * NP + c.pix] = N0;
-    P[(LP_N0 + 1) * NP + c.pix] = N1;
-    P[(LP_N0 + 2) * NP + c.pix] = N2;
+    P[LP_N0 * NP + c.pix] = Cbn.y;
+    P[(LP_N0 + 1) * NP + c.pix] = N12.x;
+    P[(LP_N0 + 2) * NP + c.pix] = N12.y;
   }
 }
 
