@@ -82,9 +82,9 @@ __device__ inline float quad(float a, float b, float c, float dx, float dy) {
 
 // The same with a fixed rounding sequence: the forward and the backward both
 // evaluate alpha through it, so they take identical alpha >= alpha_min decisions.
-__device__ inline float splat_sigma(float a, float b, float c, float dx, float dy) {
-  return __fmaf_rn(b, __fmul_rn(dx, dy),
-                   __fmul_rn(0.5f, __fmaf_rn(a, __fmul_rn(dx, dx), __fmul_rn(c, __fmul_rn(dy, dy)))));
+// d = (dx, dy), d2 = (dx^2, dy^2) (each product rounded once).
+__device__ inline float splat_sigma(float a, float b, float c, float2 d, float2 d2) {
+  return __fmaf_rn(b, __fmul_rn(d.x, d.y), __fmul_rn(0.5f, __fmaf_rn(a, d2.x, __fmul_rn(c, d2.y))));
 }
 
 // Minimum of sigma over the rectangle [X0, X1] x [Y0, Y1] (pixel-centre
@@ -174,6 +174,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   const float4* rec = at<float4>(ws, L.rec);
   const float amin = fd->alpha_min, amax = fd->alpha_max, tmin = fd->T_min, tmed = fd->median_T;
   const float fpx = c.px + 0.5f, fpy = c.py + 0.5f;
+  const float2 nfp = make_float2(-fpx, -fpy);
   const int lane = threadIdx.x & 31;
   const SubRect R = sub_rect(c.x0, c.y0, fd->tile_w / kSubW, sub);
 
@@ -210,8 +211,9 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       if (done) continue;
       ++evals;
       const float4 a = my[0][j], b = my[1][j];
-      const float dx = a.x - fpx, dy = a.y - fpy;
-      const float sig = splat_sigma(a.z, a.w, b.x, dx, dy);
+      const float2 d = __fadd2_rn(make_float2(a.x, a.y), nfp);   // (dx, dy)
+      const float dx = d.x, dy = d.y;
+      const float sig = splat_sigma(a.z, a.w, b.x, d, __fmul2_rn(d, d));
       const float al = fminf(amax, __fmul_rn(b.y, __expf(-sig)));
       if (al < amin) continue;
       const float Tn = T * (1.f - al);
@@ -418,7 +420,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float2 d = __fadd2_rn(make_float2(a.x, a.y), nfp);     // (dx, dy)
       const float dx = d.x, dy = d.y;
       const float2 d2 = __fmul2_rn(d, d);                           // (dx^2, dy^2)
-      const float sig = splat_sigma(a.z, a.w, b.x, dx, dy);
+      const float sig = splat_sigma(a.z, a.w, b.x, d, d2);
       const float G = __expf(-sig);
       const float raw = __fmul_rn(b.y, G);
       const float al0 = fminf(amax, raw);
