@@ -220,13 +220,20 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       if (Tn < tmin) { done = true; continue; }
       cm |= 1u << j;
       const float w = al * T;
-      const float4 e2 = my[2][j], e3 = my[3][j];
+      const float4 e3 = my[3][j];
       const float2 w2 = make_float2(w, w);
       if (!GEO) Crg = __ffma2_rn(w2, make_float2(e3.x, e3.y), Crg);
       Cbn = __ffma2_rn(w2, make_float2(e3.z, e3.w), Cbn);   // (b, n0); b is 0 in GEO records
       N12 = __ffma2_rn(w2, make_float2(b.z, b.w), N12);
-      const float dk = e2.z + e2.x * dx + e2.y * dy;   // Eq. 4
+      // the splat's planar depth here (Eq. 4): for Eq. 23 at every contributor,
+      // otherwise only at the median one
+      auto plane_depth = [&]() {
+        const float4 e2 = my[2][j];
+        return e2.z + e2.x * dx + e2.y * dy;
+      };
+      float dk = 0.f;
       if (LOSS) {
+        dk = plane_depth();
         if (last < 0) d0 = dk;
         const float sd = dk - d0;
         Ws += w;
@@ -235,7 +242,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       }
       if (med < 0 && Tn <= tmed) {
         med = c0 + j;
-        depth = dk;
+        depth = LOSS ? dk : plane_depth();
       }
       last = c0 + j;
       T = Tn;
