@@ -325,6 +325,16 @@ gs_status gs_render_fwd_static(const gs_frame* frame, const gs_maps* maps, gs_st
 /* Synchronises `stream`, then reads the counters and sticky status. */
 gs_status gs_check(const gs_frame* frame, gs_stats* out, void* stream);
 
+/* Test hook for the device's bounded waits (the decoupled look-back of the
+ * scans and radix sorts, which poll other blocks' words): one block polls a
+ * word that nothing publishes, gives up after `spin_limit` polls (1 ..
+ * 4194304, the limit the real waits use), sets the sticky status to
+ * GS_ERR_TIMEOUT and returns, so the context stays usable.  gs_check then
+ * reports GS_ERR_TIMEOUT; the next gs_preprocess clears the status.  Uses the
+ * frame's workspace (its binning words, which the next gs_bin clears); the
+ * frame must have been prepared as for gs_preprocess. */
+gs_status gs_debug_wait_timeout(const gs_frame* frame, int32_t spin_limit, void* stream);
+
 /* Human-readable description of the calling thread's last error. */
 const char* gs_last_error_string(void);
 

@@ -400,6 +400,18 @@ gs_status gs_debug_copy(const gs_frame* frame, float* rec, int32_t* rect, int32_
   return GS_OK;
 }
 
+gs_status gs_debug_wait_timeout(const gs_frame* frame, int32_t spin_limit, void* stream) {
+  FrameDev fd;
+  Layout L;
+  gs_status st = prepare_ws(frame, fd, L);
+  if (st != GS_OK) return st;
+  if (spin_limit < 1 || spin_limit > (1 << 22))
+    return fail(GS_ERR_INVALID_ARG, "spin_limit %d outside [1, 4194304]", spin_limit);
+  cudaError_t e = launch_wait_timeout(frame->workspace, L, spin_limit, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "wait_timeout");
+  return GS_OK;
+}
+
 gs_status gs_check(const gs_frame* frame, gs_stats* out, void* stream) {
   FrameDev fd;
   Layout L;

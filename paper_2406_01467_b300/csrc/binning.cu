@@ -126,7 +126,8 @@ __device__ inline int block_ticket(int* ticket, int* s_tk) {
 // warp 0 reads the words of 32 predecessors at a time (lane l: block j - l)
 // and adds them up to the nearest P.
 __device__ inline unsigned long long block_lookback(unsigned long long* words, int blk, unsigned long long agg,
-                                                    Header* hdr, unsigned long long* s_excl) {
+                                                    Header* hdr, unsigned long long* s_excl,
+                                                    int spin_limit = kSpinLimit) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     unsigned long long* mine = words + blk;
@@ -142,7 +143,7 @@ __device__ inline unsigned long long block_lookback(unsigned long long* words, i
       const int last = pm ? __ffs(pm) - 1 : 31;                  // lanes 0..last are needed
       const unsigned need = last == 31 ? FULL : (2u << last) - 1u;
       if (zm & need) {                                           // one of them is not published yet
-        if (++spins > kSpinLimit) {
+        if (++spins > spin_limit) {
           if (lane == 0) set_status(hdr, GS_ERR_TIMEOUT);
           break;
         }
@@ -161,6 +162,21 @@ __device__ inline unsigned long long block_lookback(unsigned long long* words, i
   }
   __syncthreads();
   return *s_excl;
+}
+
+// Test hook for the bounded waits: one block runs the look-back as block 1 of a
+// scan whose block 0 never publishes its word, so the wait runs out after
+// spin_limit polls, sets GS_ERR_TIMEOUT and the kernel returns.
+__global__ void k_wait_timeout(unsigned long long* words, int spin_limit, Header* hdr) {
+  __shared__ unsigned long long s_excl;
+  if (threadIdx.x < 2) words[threadIdx.x] = 0ull;
+  __syncthreads();
+  block_lookback(words, 1, 1ull, hdr, &s_excl, spin_limit);
+}
+
+cudaError_t launch_wait_timeout(void* ws, const Layout& L, int spin_limit, cudaStream_t s) {
+  k_wait_timeout<<<1, 32, 0, s>>>(at<unsigned long long>(ws, L.scanaux + 64), spin_limit, at<Header>(ws, L.hdr));
+  return cudaGetLastError();
 }
 
 // Compaction of visible entries: (key, entry) at their rank among visible

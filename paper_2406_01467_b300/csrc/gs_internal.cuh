@@ -201,6 +201,7 @@ gs_status set_error(gs_status s, const char* fmt, ...);
 // ---- launchers (each .cu file owns its kernels) ---------------------------
 cudaError_t launch_setup(const FrameDev& fd, void* ws, const Layout& L, cudaStream_t s);
 cudaError_t launch_preprocess(void* ws, const Layout& L, const FrameDev& host_fd, cudaStream_t s);
+cudaError_t launch_wait_timeout(void* ws, const Layout& L, int spin_limit, cudaStream_t s);
 cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& host_fd, cudaStream_t s);
 cudaError_t launch_tile_order(void* ws, const Layout& L, const uint32_t* cost, int* order, cudaStream_t s);
 cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& host_fd,

@@ -291,6 +291,12 @@ class Frame:
         H, W = self.sizes[v]
         return self.dist[off:off + H * W].view(H, W), self.nloss[off:off + H * W].view(H, W)
 
+    def debug_wait_timeout(self, spin_limit: int = 1000, stream=None):
+        """Runs the device's bounded-wait test hook (a poll that nothing answers);
+        the frame's status then reads GS_ERR_TIMEOUT until the next preprocess."""
+        check(self.lib.gs_debug_wait_timeout(ctypes.byref(self.frame), int(spin_limit), _stream(stream)),
+              "gs_debug_wait_timeout")
+
     def debug(self):
         """Intermediate buffers (records, rects, sorted pairs, ranges, 2D gradients)."""
         E, P = self.n_entries, self.pair_capacity

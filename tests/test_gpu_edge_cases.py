@@ -1,13 +1,14 @@
 """More parity cases of the CUDA path against the FP64 oracle: every SH degree
 (the kernels are instantiated per degree), BF16 rows that are not a multiple
-of 16 bytes, and a splat whose rectangle covers the whole image."""
+of 16 bytes, a splat whose rectangle covers the whole image, and the bounded
+device waits' timeout status."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from oracle import binning
-from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, scenes
+from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, _lib, scenes
 from tests._util import _same_ranges, AMBIG_MARGIN, compare_maps, gpu_maps_at, oracle_params
 
 pytestmark = pytest.mark.gpu
@@ -107,3 +108,21 @@ def test_splat_covering_the_whole_image():
         r = dec["rect"][-1]
         assert dec["valid"][-1] and r[0] == 0 and r[1] == cam.width - 1 and r[2] == 0 and r[3] == cam.height - 1
         _check_all(sc, cam, p, fr, seed=50)
+
+
+def test_bounded_wait_reports_timeout_and_the_context_stays_usable():
+    # a device wait on a word that nothing publishes gives up after its poll
+    # limit, sets GS_ERR_TIMEOUT and returns: no hang, no fault
+    sc, cam = scenes.tiny_scene(500, seed=14), scenes.tiny_camera()
+    p = RenderParams()
+    fr = _frame(sc, cam, p)
+    before = [t.clone() for t in fr.view_maps(0)]
+    assert fr.stats().status == 0
+    fr.debug_wait_timeout(1000)
+    torch.cuda.synchronize()
+    assert fr.stats().status == _lib.GS_ERR_TIMEOUT
+    fr.forward()   # the next frame clears the status and renders as before
+    torch.cuda.synchronize()
+    assert fr.stats().status == 0
+    for a, b in zip(before, fr.view_maps(0)):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)
