@@ -50,7 +50,7 @@ typedef enum {
   GS_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is out of range */
   GS_ERR_CAPACITY = 2,    /* more (tile, Gaussian) pairs than pair_capacity */
   GS_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
-  GS_ERR_TIMEOUT = 4,     /* a bounded device wait ran out (radix-sort look-back) */
+  GS_ERR_TIMEOUT = 4,     /* a bounded device wait ran out (scan / radix-sort look-back) */
   GS_ERR_NUMERIC = 5      /* non-finite inputs; those Gaussians were culled */
 } gs_status;
 
