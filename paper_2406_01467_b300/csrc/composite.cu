@@ -26,9 +26,12 @@
 //
 // Backward replays each pixel from its last contributor toward the front,
 // recovering T by division (alpha <= alpha_max < 1) and the colour / normal
-// "behind" sums recursively; nothing per (pixel, splat) is stored.  Each warp
-// reduces the 15 per-splat gradients of its 32 pixels with a reduce-scatter
-// through shared memory and issues one vector of atomics.
+// "behind" sums recursively; nothing per (pixel, splat) is stored.  It replays
+// only the records the forward marked as blended by some pixel of the warp's
+// block, two per round.  Each warp reduces the 15 per-splat sums of its 32
+// pixels (one shuffle fold, then a transpose through shared memory) and issues
+// one atomic per sum; the sums are linear in the splat's conic, p and opacity,
+// which the preprocess backward applies once per entry.
 // Eq. 23 with constant weights adds dL/dd_k = 4 w_k W (d_k - mean) to each
 // contributor's planar depth; Eq. 24 enters through the map gradients of
 // alpha, normal and depth that the normal-consistency backward stored.
