@@ -151,12 +151,14 @@ template <int N> __device__ inline void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 // A chunk buffer is slot-major ([4][32] float4): lane l's 16-byte pieces sit
-// 512 bytes apart, so per-lane accesses are free of bank conflicts.
+// 512 bytes apart, so per-lane accesses are free of bank conflicts.  The depth
+// plane (piece 2) is staged only when every contributor's depth is needed.
+template <bool PLANE>
 __device__ inline void stage_record(float4 (*chunk)[32], int lane, const float4* r) {
   const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(&chunk[0][lane]));
   cp_async16(dst, r);
   cp_async16(dst + 512, r + 1);
-  cp_async16(dst + 1024, r + 2);
+  if (PLANE) cp_async16(dst + 1024, r + 2);
   cp_async16(dst + 1536, r + 3);
 }
 
@@ -193,13 +195,13 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   int cur = 0;
   uint32_t e_next = 0;   // entry of this lane's record in the chunk after the one in flight
   if (range.x < range.y) {
-    if (range.x + lane < range.y) stage_record(buf[0], lane, rec + 4 * (int64_t)__ldg(pval + range.x + lane));
+    if (range.x + lane < range.y) stage_record<LOSS>(buf[0], lane, rec + 4 * (int64_t)__ldg(pval + range.x + lane));
     cp_async_commit();
     if (range.x + 32 + lane < range.y) e_next = __ldg(pval + range.x + 32 + lane);
   }
   for (int c0 = range.x; c0 < range.y; c0 += 32) {
     if (__all_sync(kFull, done)) break;
-    if (c0 + 32 + lane < range.y) stage_record(buf[cur ^ 1], lane, rec + 4 * (int64_t)e_next);
+    if (c0 + 32 + lane < range.y) stage_record<LOSS>(buf[cur ^ 1], lane, rec + 4 * (int64_t)e_next);
     cp_async_commit();
     if (c0 + 64 + lane < range.y) e_next = __ldg(pval + c0 + 64 + lane);
     cp_async_wait<1>();     // this lane's copies of chunk c0 have landed
@@ -228,15 +230,12 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       if (!GEO) Crg = __ffma2_rn(w2, make_float2(e3.x, e3.y), Crg);
       Cbn = __ffma2_rn(w2, make_float2(e3.z, e3.w), Cbn);   // (b, n0); b is 0 in GEO records
       N12 = __ffma2_rn(w2, make_float2(b.z, b.w), N12);
-      // the splat's planar depth here (Eq. 4): for Eq. 23 at every contributor,
-      // otherwise only at the median one
-      auto plane_depth = [&]() {
-        const float4 e2 = my[2][j];
-        return e2.z + e2.x * dx + e2.y * dy;
-      };
+      // the splat's planar depth here (Eq. 4): for Eq. 23 at every contributor;
+      // otherwise only the median's, after the walk
       float dk = 0.f;
       if (LOSS) {
-        dk = plane_depth();
+        const float4 e2 = my[2][j];
+        dk = e2.z + e2.x * dx + e2.y * dy;
         if (last < 0) d0 = dk;
         const float sd = dk - d0;
         Ws += w;
@@ -245,7 +244,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       }
       if (med < 0 && Tn <= tmed) {
         med = c0 + j;
-        depth = LOSS ? dk : plane_depth();
+        if (LOSS) depth = dk;
       }
       last = c0 + j;
       T = Tn;
@@ -262,9 +261,12 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   __syncwarp();
   blended += nblend;
   if (!c.inside) return;
-  if (med < 0 && last >= 0) {   // median never reached: depth of the last contributor
-    med = last;
-    const float4* r = rec + 4 * (int64_t)pval[last];
+  // the median's depth (Eq. 4), unless the walk computed it (LOSS); median
+  // never reached: the last contributor's
+  const bool have = LOSS && med >= 0;
+  if (med < 0) med = last;
+  if (!have && med >= 0) {
+    const float4* r = rec + 4 * (int64_t)pval[med];
     const float4 a = r[0], e2 = r[2];
     depth = e2.z + e2.x * (a.x - fpx) + e2.y * (a.y - fpy);
   }
