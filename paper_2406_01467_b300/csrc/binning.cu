@@ -482,11 +482,57 @@ cudaError_t launch_tile_order(void* ws, const Layout& L, const uint32_t* cost, i
 // scatters.  Blocks take their tile of keys in the order they start (a ticket
 // counter), so a block only ever waits for blocks that are already running;
 // every wait is bounded and sets GS_ERR_TIMEOUT if it runs out.
+//
+// kBallot finds the lanes of a warp holding the same digit (its peer mask)
+// with one ballot per digit bit (the last pass's digit may have fewer than 8);
+// otherwise a digit shared by the whole warp needs no matching and the others
+// take `match.any`, which costs about 36 SM cycles per warp-wide call.
+// The depth sort (one wave of blocks: each block's latency is the pass's time)
+// runs two blocks per SM with ballots, 128 registers holding a thread's keys,
+// values and ranks without spilling; the tile sort (several waves: throughput)
+// runs three blocks per SM with `match.any`, whose ranking needs fewer
+// registers.  The look-back reads 4 predecessors' words per poll.
 // ---------------------------------------------------------------------------
+constexpr int kLookWindow = 4;
 
-__global__ void __launch_bounds__(kSortThreads, 3)
+// Exclusive prefix of digit d over the blocks before blk: the predecessors'
+// words are read kLookWindow at a time, nearest first, and added up to the
+// nearest P; a window with an unpublished word before that P is read again.
+__device__ inline uint32_t digit_lookback(const unsigned long long* look, int blk, int d, Header* hdr) {
+  uint32_t excl = 0;
+  int j = blk - 1, spins = 0;
+  while (j >= 0) {
+    unsigned long long f[kLookWindow];
+#pragma unroll
+    for (int q = 0; q < kLookWindow; ++q)   // before block 0: a zero inclusive prefix
+      f[q] = j - q >= 0 ? ld_relaxed(look + (int64_t)(j - q) * kRadix + d) : kFlagP;
+    int qp = kLookWindow;
+#pragma unroll
+    for (int q = kLookWindow - 1; q >= 0; --q)
+      if ((f[q] & kFlagMask) == kFlagP) qp = q;
+    bool ready = true;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < kLookWindow; ++q)
+      if (q <= qp) {
+        ready = ready && (f[q] & kFlagMask) != 0;
+        sum += (uint32_t)f[q];
+      }
+    if (!ready) {
+      if (++spins > kSpinLimit) { set_status(hdr, GS_ERR_TIMEOUT); break; }
+      continue;
+    }
+    excl += sum;
+    if (qp < kLookWindow) break;
+    j -= kLookWindow;
+  }
+  return excl;
+}
+
+template <int kMinBlocks, bool kBallot>
+__global__ void __launch_bounds__(kSortThreads, kMinBlocks)
 k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-           uint32_t* __restrict__ vout, const unsigned long long* count_ptr, int64_t cap, int pass,
+           uint32_t* __restrict__ vout, const unsigned long long* count_ptr, int64_t cap, int pass, int dbits,
            const uint32_t* __restrict__ ghist, unsigned long long* __restrict__ look, int* ticket, Header* hdr) {
   // [half][warp][digit] running digit counts of a warp's two halves of items
   // (rounds 0-7 and 8-15: two independent chains), then [0]: the warps' bases
@@ -524,9 +570,23 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   // in two counter sets
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    const int d = li0 + 32 * r < nloc ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
-    // a digit shared by the whole warp needs no matching
-    rank[r] = __all_sync(FULL, d == __shfl_sync(FULL, d, 0)) ? FULL : __match_any_sync(FULL, d);
+    const bool valid = li0 + 32 * r < nloc;
+    const uint32_t d = (k[r] >> shift) & (kRadix - 1);
+    const int dv = valid ? (int)d : kRadix;
+    if (kBallot) {
+      unsigned peers = __ballot_sync(FULL, valid);   // lanes past the end match nobody
+#pragma unroll
+      for (int b = 0; b < kRadixBits; ++b) {
+        if (b < dbits) {
+          const bool bit = (d >> b) & 1u;
+          const unsigned m = __ballot_sync(FULL, bit);
+          peers &= bit ? m : ~m;
+        }
+      }
+      rank[r] = peers;
+    } else {   // a digit shared by the whole warp needs no matching
+      rank[r] = __all_sync(FULL, dv == __shfl_sync(FULL, dv, 0)) ? FULL : __match_any_sync(FULL, dv);
+    }
   }
   constexpr int kHalf = kSortItems / 2;
 #pragma unroll
@@ -566,18 +626,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   // decoupled look-back: keys of digit d in the blocks before this one
   uint32_t excl = 0;
   if (blk > 0) {
-    int j = blk - 1, spins = 0;
-    for (;;) {
-      const unsigned long long f = ld_relaxed(look + (int64_t)j * kRadix + d);
-      const unsigned long long st = f & kFlagMask;
-      if (st == 0) {
-        if (++spins > kSpinLimit) { set_status(hdr, GS_ERR_TIMEOUT); break; }
-        continue;
-      }
-      excl += (uint32_t)f;
-      if (st == kFlagP || j == 0) break;
-      --j;
-    }
+    excl = digit_lookback(look, blk, d, hdr);
     st_relaxed(mine, kFlagP | (excl + cnt));
   }
   s_gbase[d] = dbase + excl;
@@ -603,6 +652,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
 // Sorts (k0, v0) by the low `bits` bits of the keys, whose digit histograms are
 // already in aux; the result ends in (k0, v0) after an even number of 8-bit
 // passes, else in (k1, v1).
+template <int kMinBlocks, bool kBallot>
 static cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                               const unsigned long long* count, int64_t cap, int nb, int bits, void* aux,
                               size_t aux_bytes, Header* hdr, cudaStream_t s) {
@@ -613,8 +663,10 @@ static cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t
   (void)aux_bytes;   // cleared by the binning's single memset
   uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
   for (int p = 0; p < passes; ++p) {
-    k_onesweep<<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, cap, p, ghist, look + (int64_t)p * nb * kRadix,
-                                           tickets + p, hdr);
+    // keys are below 2^bits: the last pass's digit has its remaining bits only
+    const int dbits = bits - kRadixBits * p < kRadixBits ? bits - kRadixBits * p : kRadixBits;
+    k_onesweep<kMinBlocks, kBallot><<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, cap, p, dbits, ghist,
+                                           look + (int64_t)p * nb * kRadix, tickets + p, hdr);
     uint32_t* t;
     t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
@@ -648,7 +700,7 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   k_compact<<<L.nb_E, kSortThreads, 0, s>>>(key, L.E, vk0, vv0, at<uint32_t>(ws, L.sortaux[0]), scan_words,
                                            scan_ticket, &hdr->n_vis, hdr);
   // 2. depth sort: 31 bits (z > 0, so the sign bit is clear)
-  cudaError_t err = radix_sort(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, at<void>(ws, L.sortaux[0]),
+  cudaError_t err = radix_sort<2, true>(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, at<void>(ws, L.sortaux[0]),
                                L.sortaux_bytes[0], hdr, s);
   if (err != cudaSuccess) return err;
   // 3. pair offsets (the pair count and the capacity check)
@@ -667,7 +719,7 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
                                      pair_off, L.Pcap, pt0, pv0, chunk_first, n_chunks, tile_passes,
                                      at<uint32_t>(ws, L.sortaux[1]));
   // 5. tile sort
-  err = radix_sort(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, at<void>(ws, L.sortaux[1]),
+  err = radix_sort<3, false>(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, at<void>(ws, L.sortaux[1]),
                    L.sortaux_bytes[1], hdr, s);
   if (err != cudaSuccess) return err;
   uint32_t* ptile = at<uint32_t>(ws, L.ptile_final);
