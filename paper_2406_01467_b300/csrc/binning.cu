@@ -487,11 +487,12 @@ cudaError_t launch_tile_order(void* ws, const Layout& L, const uint32_t* cost, i
 // with one ballot per digit bit (the last pass's digit may have fewer than 8);
 // otherwise a digit shared by the whole warp needs no matching and the others
 // take `match.any`, which costs about 36 SM cycles per warp-wide call.
-// The depth sort (one wave of blocks: each block's latency is the pass's time)
-// runs two blocks per SM with ballots, 128 registers holding a thread's keys,
-// values and ranks without spilling; the tile sort (several waves: throughput)
-// runs three blocks per SM with `match.any`, whose ranking needs fewer
-// registers.  The look-back reads 4 predecessors' words per poll.
+// A pass over a full 8-bit digit (the depth sort's four passes, the tile
+// sort's first: digits spread over many values) runs two blocks per SM with
+// ballots, 128 registers holding a thread's keys, values and ranks without
+// spilling; the tile sort's last pass (a few high bits of the tile index,
+// often shared by a whole warp) runs three blocks per SM with `match.any`.
+// The look-back reads 4 predecessors' words per poll.
 // ---------------------------------------------------------------------------
 constexpr int kLookWindow = 4;
 
@@ -652,7 +653,6 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
 // Sorts (k0, v0) by the low `bits` bits of the keys, whose digit histograms are
 // already in aux; the result ends in (k0, v0) after an even number of 8-bit
 // passes, else in (k1, v1).
-template <int kMinBlocks, bool kBallot>
 static cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                               const unsigned long long* count, int64_t cap, int nb, int bits, void* aux,
                               size_t aux_bytes, Header* hdr, cudaStream_t s) {
@@ -665,8 +665,11 @@ static cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t
   for (int p = 0; p < passes; ++p) {
     // keys are below 2^bits: the last pass's digit has its remaining bits only
     const int dbits = bits - kRadixBits * p < kRadixBits ? bits - kRadixBits * p : kRadixBits;
-    k_onesweep<kMinBlocks, kBallot><<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, cap, p, dbits, ghist,
-                                           look + (int64_t)p * nb * kRadix, tickets + p, hdr);
+    unsigned long long* lp = look + (int64_t)p * nb * kRadix;
+    if (dbits == kRadixBits)
+      k_onesweep<2, true><<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, cap, p, dbits, ghist, lp, tickets + p, hdr);
+    else
+      k_onesweep<3, false><<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, cap, p, dbits, ghist, lp, tickets + p, hdr);
     uint32_t* t;
     t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
@@ -700,7 +703,7 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   k_compact<<<L.nb_E, kSortThreads, 0, s>>>(key, L.E, vk0, vv0, at<uint32_t>(ws, L.sortaux[0]), scan_words,
                                            scan_ticket, &hdr->n_vis, hdr);
   // 2. depth sort: 31 bits (z > 0, so the sign bit is clear)
-  cudaError_t err = radix_sort<2, true>(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, at<void>(ws, L.sortaux[0]),
+  cudaError_t err = radix_sort(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, at<void>(ws, L.sortaux[0]),
                                L.sortaux_bytes[0], hdr, s);
   if (err != cudaSuccess) return err;
   // 3. pair offsets (the pair count and the capacity check)
@@ -719,7 +722,7 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
                                      pair_off, L.Pcap, pt0, pv0, chunk_first, n_chunks, tile_passes,
                                      at<uint32_t>(ws, L.sortaux[1]));
   // 5. tile sort
-  err = radix_sort<3, false>(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, at<void>(ws, L.sortaux[1]),
+  err = radix_sort(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, at<void>(ws, L.sortaux[1]),
                    L.sortaux_bytes[1], hdr, s);
   if (err != cudaSuccess) return err;
   uint32_t* ptile = at<uint32_t>(ws, L.ptile_final);
