@@ -33,14 +33,19 @@ constexpr int kMaxPasses = 4;
 
 // Digit histograms of the radix sort's passes, accumulated by the kernel that
 // writes the keys: h[pass][digit] in shared memory, then added to the global
-// histograms.  Warp-collective (all 32 lanes call it): a digit shared by all of
-// the warp's valid keys (the high digits mostly are) costs one atomic.
-__device__ inline void hist_keys(uint32_t (*h)[kRadix], int passes, uint32_t key, bool valid) {
+// histograms.  Warp-collective (all 32 lanes call it).  From pass `tested` on
+// (the high digits) a digit shared by all of the warp's valid keys costs one
+// atomic; the lower digits are spread out and go straight to the atomics.
+__device__ inline void hist_keys(uint32_t (*h)[kRadix], int passes, uint32_t key, bool valid, int tested) {
   const unsigned vm = __ballot_sync(FULL, valid);
   if (vm == 0) return;
   const int leader = __ffs(vm) - 1;
   for (int p = 0; p < passes; ++p) {
     const int d = (int)((key >> (kRadixBits * p)) & (kRadix - 1));
+    if (p < tested) {
+      if (valid) atomicAdd(&h[p][d], 1u);
+      continue;
+    }
     const int d0 = __shfl_sync(FULL, d, leader);
     if (__all_sync(FULL, !valid || d == d0)) {
       if ((int)(threadIdx.x & 31) == leader) atomicAdd(&h[p][d0], (uint32_t)__popc(vm));
@@ -220,7 +225,7 @@ k_compact(const uint32_t* __restrict__ key, int64_t E, uint32_t* __restrict__ ok
       oval[pos] = (uint32_t)WarpItems::index(base, r);
     }
     off += __popc(bal);
-    hist_keys(s_h, kMaxPasses, k[r], v);
+    hist_keys(s_h, kMaxPasses, k[r], v, kMaxPasses - 1);
   }
   hist_flush(s_h, kMaxPasses, ghist);
 }
@@ -314,8 +319,10 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
        const short4* __restrict__ rect, const uint32_t* __restrict__ pair_off, int64_t cap,
        uint32_t* __restrict__ ptile, uint32_t* __restrict__ pval, const uint32_t* __restrict__ chunk_first,
        int64_t n_chunks, int tile_passes, uint32_t* __restrict__ ghist) {
-  __shared__ uint32_t s_off[kEmitChunk + 1], s_ent[kEmitChunk + 1];
-  __shared__ short4 s_rc[kEmitChunk + 1];
+  // per entry of the slice: its first pair, and (entry, first tile of its
+  // rectangle, rectangle width | tile row length << 16, 1 / width)
+  __shared__ uint32_t s_off[kEmitChunk + 1];
+  __shared__ uint4 s_ent[kEmitChunk + 1];
   __shared__ uint4 s_idx[kEmitChunk / 8];   // per pair: its entry's slot in s_off (uint16, 8 per piece)
   __shared__ int64_t s_k[2];
   __shared__ uint32_t s_h[kMaxPasses][kRadix];   // the tile sort's digit histograms
@@ -345,8 +352,17 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       const uint32_t e = __ldg(sval + k0 + i);
       s_off[i] = __ldg(pair_off + k0 + i);
-      s_ent[i] = e;
-      s_rc[i] = rect[e];
+      const short4 rc = rect[e];
+      int rowlen = tiles_x0, toff = 0;
+      if (nv > 1) {
+        const int vi = find_view(fd->entry_off, nv, (int64_t)e);
+        rowlen = fd->views[vi].tiles_x;
+        toff = fd->tile_off[vi];
+      }
+      const int tx0 = rc.x >> sx, ty0 = rc.z >> sy;
+      const uint32_t nx = (uint32_t)((rc.y >> sx) - tx0 + 1);
+      s_ent[i] = make_uint4(e, (uint32_t)(toff + ty0 * rowlen + tx0), nx | ((uint32_t)rowlen << 16),
+                            __float_as_uint(__frcp_rn((float)nx)));
     }
     __syncthreads();
     // each thread finds the entry of its first of 8 consecutive pairs by
@@ -381,23 +397,20 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
       uint32_t t = 0;
       if (ok) {
         const int lo = idx[i];
-        const uint32_t e = s_ent[lo];
-        const short4 rc = s_rc[lo];
-        const int tx0 = rc.x >> sx, ty0 = rc.z >> sy;
-        const uint32_t nx = (uint32_t)((rc.y >> sx) - tx0 + 1);
-        const uint32_t local = (uint32_t)(p0 + i) - s_off[lo];
-        const uint32_t ty = local / nx, tx = local - ty * nx;
-        int rowlen = tiles_x0, toff = 0;
-        if (nv > 1) {
-          const int vi = find_view(fd->entry_off, nv, (int64_t)e);
-          rowlen = fd->views[vi].tiles_x;
-          toff = fd->tile_off[vi];
-        }
-        t = (uint32_t)(toff + (ty0 + (int)ty) * rowlen + tx0 + (int)tx);
+        const uint4 en = s_ent[lo];
+        const int nx = (int)(en.z & 0xFFFFu), rowlen = (int)(en.z >> 16);
+        const int local = (int)((uint32_t)(p0 + i) - s_off[lo]);
+        // row and column of the pair in its rectangle: a reciprocal estimate of
+        // local / nx, within one of the quotient while local < 2^23 (a view has
+        // at most 2^23 tiles), then one integer correction step
+        int ty = (int)(((float)local + 0.5f) * __uint_as_float(en.w));
+        int tx = local - ty * nx;
+        if (tx < 0) { --ty; tx += nx; } else if (tx >= nx) { ++ty; tx -= nx; }
+        t = en.y + (uint32_t)(ty * rowlen + tx);
         ptile[p0 + i] = t;
-        pval[p0 + i] = e;
+        pval[p0 + i] = en.x;
       }
-      hist_keys(s_h, tile_passes, t, ok);
+      hist_keys(s_h, tile_passes, t, ok, 1);
     }
   }
   hist_flush(s_h, tile_passes, ghist);
