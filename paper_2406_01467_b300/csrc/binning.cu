@@ -629,17 +629,20 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   uint32_t c[8], cnt = 0;
   for (int i = 0; i < 8; ++i) { c[i] = (uint32_t)s_wc[0][i][d] + s_wc[1][i][d]; cnt += c[i]; }
   unsigned long long* mine = look + (int64_t)blk * kRadix + d;
-  st_relaxed(mine, (blk == 0 ? kFlagP : kFlagA) | cnt);   // successors may start looking
+  // a digit no key holds (most of a narrow or concentrated digit's values)
+  // needs neither the word nor the look-back: every block skips it alike
+  const uint32_t gcnt = ghist[pass * kRadix + d];
+  if (gcnt) st_relaxed(mine, (blk == 0 ? kFlagP : kFlagA) | cnt);   // successors may start looking
   // block-local exclusive scan over (digit, warp) in digit-major order, and the
   // digit's start in the whole key set (exclusive scan of the global histogram)
   const uint32_t start = block_exclusive_scan(cnt, s_warp, nullptr);
-  const uint32_t dbase = block_exclusive_scan(ghist[pass * kRadix + d], s_warp, nullptr);
+  const uint32_t dbase = block_exclusive_scan(gcnt, s_warp, nullptr);
   s_dstart[d] = start;
   uint32_t run = start;
   for (int i = 0; i < 8; ++i) { s_wc[0][i][d] = (uint16_t)run; run += c[i]; }   // bases <= 4096
   // decoupled look-back: keys of digit d in the blocks before this one
   uint32_t excl = 0;
-  if (blk > 0) {
+  if (blk > 0 && gcnt) {
     excl = digit_lookback(look, blk, d, hdr);
     st_relaxed(mine, kFlagP | (excl + cnt));
   }
