@@ -91,28 +91,23 @@ __device__ inline float splat_sigma(float a, float b, float c, float2 d, float2 
 }
 
 // Minimum of sigma over the rectangle [X0, X1] x [Y0, Y1] (pixel-centre
-// coordinates): zero if the centre is inside, else the least of the four
-// edges' minima (each a 1D convex quadratic, clamped to the edge).
+// coordinates): zero if the centre is inside.  Otherwise the minimum lies on
+// an edge facing the centre: sigma grows along the segment from the centre to
+// any point of the rectangle (it scales with the square of the distance along
+// it), and that segment enters the rectangle through an edge whose outside
+// holds the centre.  So one vertical and one horizontal edge suffice (the
+// facing one where there is one; either edge otherwise, which only adds a
+// candidate), each a 1D convex quadratic clamped to the edge.
 __device__ inline float rect_min_sigma(float u, float v, float a, float b, float c, float ia,
                                        float ic, float X0, float X1, float Y0, float Y1) {
   if (u >= X0 && u <= X1 && v >= Y0 && v <= Y1) return 0.f;
-  float best = 3.4e38f;
-  // vertical edges x = X: dx fixed, dy minimises c dy + b dx = 0
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const float X = e ? X1 : X0;
-    const float dx = u - X;
-    const float y = fminf(fmaxf(v + b * dx * ic, Y0), Y1);
-    best = fminf(best, quad(a, b, c, dx, v - y));
-  }
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const float Y = e ? Y1 : Y0;
-    const float dy = v - Y;
-    const float x = fminf(fmaxf(u + b * dy * ia, X0), X1);
-    best = fminf(best, quad(a, b, c, u - x, dy));
-  }
-  return best;
+  // vertical edge x = X: dx fixed, dy minimises c dy + b dx = 0
+  const float dx = u - (u < X0 ? X0 : X1);
+  const float y = fminf(fmaxf(v + b * dx * ic, Y0), Y1);
+  // horizontal edge y = Y
+  const float dy = v - (v < Y0 ? Y0 : Y1);
+  const float x = fminf(fmaxf(u + b * dy * ia, X0), X1);
+  return fminf(quad(a, b, c, dx, v - y), quad(a, b, c, u - x, dy));
 }
 
 // Rectangle of warp w's pixel centres inside the tile starting at (x0, y0).
