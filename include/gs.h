@@ -283,7 +283,8 @@ gs_status gs_adam_step(float* params, float* grads, float* m, float* v, int64_t 
 
 /* Intermediate results for tests and tools, copied to caller device buffers on
  * `stream`; any pointer may be NULL.  rec: [n_entries][16] FP32 per-entry
- * records (u, v, conic a b c, opacity, n1 n2, p0 p1, z, 0, r g b, n0);
+ * records (u, v, a' b' c', opacity, n1 n2, p0 p1, z, 0, r g b, n0), where
+ * (a', b', c') = log2(e) (a / 2, b, c / 2) for the conic (a, b, c);
  * rect: [n_entries][4] int32 pixel rectangle (i0, i1, j0, j1), (0,-1,0,-1)
  * when culled; pair_tile/pair_entry: [pair_capacity] int32 sorted pairs;
  * ranges: [total tiles][2] int32.  grad2d: [n_entries][16] FP32 per-entry sums

@@ -4,6 +4,9 @@
 // through shared memory one batch of records at a time:
 //   Delta = (u_c - u, v_c - v); sigma = 1/2 Delta^T conic Delta;
 //   alpha = min(alpha_max, o exp(-sigma)), skipped below alpha_min;
+//   (the record holds the conic times log2(e), its diagonal halved, so that
+//   s = sigma log2(e) takes two multiplies and two fused multiply-adds and
+//   exp(-sigma) = 2^-s one ex2)
 //   stop before T (1 - alpha) < T_min;  w = alpha T;
 //   colour += w rgb (Eq. 3); normal += w n (Eq. 22);
 //   depth = z_c + p Delta (Eq. 4) of the first splat with T' <= median_T
@@ -12,8 +15,9 @@
 //
 // Each warp owns an 8x4 block of the tile's pixels and walks the tile's list on
 // its own.  A record is evaluated only if the splat can reach the block: the
-// minimum of sigma over the block's rectangle of pixel centres (exact, over its
-// four edges) is at most sigma_cut = ln(o / alpha_min) plus a small margin.  A
+// minimum of sigma over the block's rectangle of pixel centres (exact, over the
+// two edges facing the splat's centre) is at most sigma_cut = ln(o / alpha_min)
+// plus a small margin.  A
 // splat skipped this way is one every pixel of the block would have skipped by
 // the alpha test, so the maps are the same as without the culling.
 //
@@ -78,16 +82,24 @@ __device__ inline TileCtx tile_ctx(const FrameDev* fd, int tile, int sub) {
   return c;
 }
 
-// sigma at offset (dx, dy) from the centre.
+// s = sigma log2(e) at offset (dx, dy) from the centre, from the record's
+// scaled conic (a, b, c) = log2(e) (conic_00 / 2, conic_01, conic_11 / 2).
 __device__ inline float quad(float a, float b, float c, float dx, float dy) {
-  return 0.5f * (a * dx * dx + c * dy * dy) + b * dx * dy;
+  return a * dx * dx + c * dy * dy + b * dx * dy;
 }
 
 // The same with a fixed rounding sequence: the forward and the backward both
 // evaluate alpha through it, so they take identical alpha >= alpha_min decisions.
 // d = (dx, dy), d2 = (dx^2, dy^2) (each product rounded once).
-__device__ inline float splat_sigma(float a, float b, float c, float2 d, float2 d2) {
-  return __fmaf_rn(b, __fmul_rn(d.x, d.y), __fmul_rn(0.5f, __fmaf_rn(a, d2.x, __fmul_rn(c, d2.y))));
+__device__ inline float splat_s(float a, float b, float c, float2 d, float2 d2) {
+  return __fmaf_rn(b, __fmul_rn(d.x, d.y), __fmaf_rn(a, d2.x, __fmul_rn(c, d2.y)));
+}
+
+// 2^x (PTX ex2.approx: relative error near 2^-22): exp(-sigma) = 2^-s.
+__device__ inline float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // Minimum of sigma over the rectangle [X0, X1] x [Y0, Y1] (pixel-centre
@@ -101,7 +113,7 @@ __device__ inline float splat_sigma(float a, float b, float c, float2 d, float2 
 __device__ inline float rect_min_sigma(float u, float v, float a, float b, float c, float ia,
                                        float ic, float X0, float X1, float Y0, float Y1) {
   if (u >= X0 && u <= X1 && v >= Y0 && v <= Y1) return 0.f;
-  // vertical edge x = X: dx fixed, dy minimises c dy + b dx = 0
+  // vertical edge x = X: dx fixed, dy minimises 2 c dy + b dx = 0 (ic = 1 / 2c)
   const float dx = u - (u < X0 ? X0 : X1);
   const float y = fminf(fmaxf(v + b * dx * ic, Y0), Y1);
   // horizontal edge y = Y
@@ -126,12 +138,13 @@ __device__ inline SubRect sub_rect(int x0, int y0, int sub_per_row, int sub) {
 }
 
 // Can the splat (first two record float4s) reach any pixel of the rectangle?
-// sigma_cut: beyond it alpha < alpha_min, with a margin (1e-4 relative and
-// absolute) far above the error of the FP32 operations and of __logf, so the
-// test only ever skips splats the alpha test rejects at every pixel.
+// s_cut = log2(o / alpha_min): beyond it alpha < alpha_min, with a margin
+// (1e-4 relative, 1.5e-4 absolute) far above the error of the FP32 operations
+// and of __log2f, so the test only ever skips splats the alpha test rejects at
+// every pixel.
 __device__ inline bool reaches(const float4& f0, const float4& f1, const SubRect& R, float amin) {
-  const float ia = __fdividef(1.f, f0.z), ic = __fdividef(1.f, f1.x);
-  const float cut = __logf(__fdividef(f1.y, amin)) * 1.0001f + 1e-4f;
+  const float ia = __fdividef(0.5f, f0.z), ic = __fdividef(0.5f, f1.x);
+  const float cut = __log2f(__fdividef(f1.y, amin)) * 1.0001f + 1.5e-4f;
   return rect_min_sigma(f0.x, f0.y, f0.z, f0.w, f1.x, ia, ic, R.X0, R.X1, R.Y0, R.Y1) <= cut;
 }
 
@@ -213,8 +226,8 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float4 a = my[0][j], b = my[1][j];
       const float2 d = __fadd2_rn(make_float2(a.x, a.y), nfp);   // (dx, dy)
       const float dx = d.x, dy = d.y;
-      const float sig = splat_sigma(a.z, a.w, b.x, d, __fmul2_rn(d, d));
-      const float al = fminf(amax, __fmul_rn(b.y, __expf(-sig)));
+      const float sl = splat_s(a.z, a.w, b.x, d, __fmul2_rn(d, d));
+      const float al = fminf(amax, __fmul_rn(b.y, ex2(-sl)));
       if (al < amin) continue;
       const float Tn = T * (1.f - al);
       if (Tn < tmin) { done = true; continue; }
@@ -427,8 +440,8 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float2 d = __fadd2_rn(make_float2(a.x, a.y), nfp);     // (dx, dy)
       const float dx = d.x, dy = d.y;
       const float2 d2 = __fmul2_rn(d, d);                           // (dx^2, dy^2)
-      const float sig = splat_sigma(a.z, a.w, b.x, d, d2);
-      const float G = __expf(-sig);
+      const float sl = splat_s(a.z, a.w, b.x, d, d2);
+      const float G = ex2(-sl);
       const float raw = __fmul_rn(b.y, G);
       const float al0 = fminf(amax, raw);
       const bool contrib = live && al0 >= amin;

@@ -20,8 +20,10 @@ constexpr int kEmitChunk = 2048;          // pairs per emission slice
 constexpr int kRadix = 1 << kRadixBits;
 
 // The record of a (view, Gaussian) entry: four float4s
-//   #0 (u, v, conic a, conic b)   #1 (conic c, opacity, n_y, n_z)
+//   #0 (u, v, a', b')             #1 (c', opacity, n_y, n_z)
 //   #2 (p0, p1, z_c, 0)           #3 (r, g, b, n_x)
+// with (a', b', c') = log2(e) (a / 2, b, c / 2) for the conic (a, b, c), so
+// that sigma log2(e) = a' dx^2 + b' dx dy + c' dy^2.
 // #0 and #1 hold everything the alpha test needs; #2 only the planar depth.
 // Slots of the per-entry 2D-gradient row the compositing backward accumulates
 // (gs = dL/dsigma, sd = dL/dd per pixel; the preprocess backward turns the

@@ -427,8 +427,11 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
     }
     if (valid) {
       float4* r = rec + 4 * e;
-      r[0] = make_float4(u, v, conic[0], conic[1]);
-      r[1] = make_float4(conic[2], o, nn[1], nn[2]);
+      // the conic times log2(e), diagonal halved: the compositing evaluates
+      // sigma log2(e) directly and exp(-sigma) as a power of two
+      constexpr float kL2E = 1.44269504088896341f;   // log2(e)
+      r[0] = make_float4(u, v, conic[0] * (0.5f * kL2E), conic[1] * kL2E);
+      r[1] = make_float4(conic[2] * (0.5f * kL2E), o, nn[1], nn[2]);
       r[2] = make_float4(pp[0], pp[1], z, 0.f);
       r[3] = make_float4(rgb[0], rgb[1], rgb[2], nn[0]);
       rect[e] = make_short4((short)i0, (short)i1, (short)j0, (short)j1);

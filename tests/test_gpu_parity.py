@@ -56,9 +56,11 @@ def test_records_match_oracle_tiny():
     pre = ref["pre"]
     np.testing.assert_allclose(rec[v, 0], pre["u"][v], atol=1e-4)
     np.testing.assert_allclose(rec[v, 1], pre["v"][v], atol=1e-4)
+    # the record's conic is scaled for base-2 exponentials: log2(e) (a / 2, b, c / 2)
+    kscale = np.log2(np.e) * np.array([0.5, 1.0, 0.5])
     for k, col in enumerate((2, 3, 4)):
-        scale = np.abs(pre["conic"][v]).max(axis=1)
-        np.testing.assert_array_less(np.abs(rec[v, col] - pre["conic"][v, k]), 1e-4 * scale + 1e-9)
+        scale = np.abs(pre["conic"][v]).max(axis=1) * kscale[k]
+        np.testing.assert_array_less(np.abs(rec[v, col] - kscale[k] * pre["conic"][v, k]), 1e-4 * scale + 1e-9)
     np.testing.assert_allclose(rec[v, 5], pre["opacity"][v], rtol=1e-7)
     np.testing.assert_allclose(rec[v, 10], pre["z"][v], rtol=1e-6)
     np.testing.assert_allclose(rec[v, 8:10], pre["p"][v], atol=1e-5)
