@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "gs_internal.cuh"
+#include <cstddef>
 
 namespace gs {
 
@@ -205,16 +206,35 @@ static gs_status prepare_ws(const gs_frame* f, FrameDev& fd, Layout& L) {
   return GS_OK;
 }
 
+// Copies the used part of the frame description (the first n_views views and
+// n_scenes scenes, the first n_views + 1 offsets of each table, the scalars):
+// the parameter words are read from the constant bank, where the lanes' distinct
+// addresses serialise, so the unused view and scene slots (most of the 11 KB)
+// are left out; no kernel reads them.
 __global__ void k_setup(FrameDev fd, FrameDev* dst, Header* hdr) {
   const uint32_t* src = reinterpret_cast<const uint32_t*>(&fd);
   uint32_t* d = reinterpret_cast<uint32_t*>(dst);
-  const int nw = (int)(sizeof(FrameDev) / 4);
-  for (int i = threadIdx.x; i < nw; i += blockDim.x) d[i] = src[i];
+  const int nv = fd.n_views, ns = fd.n_scenes;
+  auto copy = [&](size_t off, size_t bytes) {
+    const int w0 = (int)(off / 4), nw = (int)(bytes / 4);
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) d[w0 + i] = src[w0 + i];
+  };
+  copy(offsetof(FrameDev, views), nv * sizeof(ViewDev));
+  copy(offsetof(FrameDev, scenes), ns * sizeof(SceneDev));
+  copy(offsetof(FrameDev, entry_off), (nv + 1) * sizeof(int64_t));
+  copy(offsetof(FrameDev, pix_off), (nv + 1) * sizeof(int64_t));
+  copy(offsetof(FrameDev, tile_off), (nv + 1) * sizeof(int32_t));
+  copy(offsetof(FrameDev, chunk_off), (nv + 1) * sizeof(int32_t));
+  copy(offsetof(FrameDev, n_views), sizeof(FrameDev) - offsetof(FrameDev, n_views));
   uint32_t* h = reinterpret_cast<uint32_t*>(hdr);
   for (int i = threadIdx.x; i < (int)(sizeof(Header) / 4); i += blockDim.x) h[i] = 0u;
 }
 
 static_assert(sizeof(FrameDev) % 4 == 0, "FrameDev must be a whole number of words");
+static_assert(sizeof(ViewDev) % 4 == 0 && sizeof(SceneDev) % 4 == 0 && offsetof(FrameDev, views) % 4 == 0 &&
+                  offsetof(FrameDev, scenes) % 4 == 0 && offsetof(FrameDev, tile_off) % 4 == 0 &&
+                  offsetof(FrameDev, chunk_off) % 4 == 0 && offsetof(FrameDev, n_views) % 4 == 0,
+              "the frame description's tables are whole words");
 static_assert(sizeof(Header) == 256, "Header is one 256-byte block");
 
 cudaError_t launch_setup(const FrameDev& fd, void* ws, const Layout& L, cudaStream_t s) {
