@@ -410,15 +410,13 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
     const uint32_t wm = cmask[k];
     if (wm == 0) continue;
     const int c0 = range.x + 32 * k;
-    if ((wm >> lane) & 1u) {
+    if ((wm >> lane) & 1u) {   // copies straight to shared memory, no registers
       const uint32_t e = pval[c0 + lane];
-      const float4* r = rec + 4 * (int64_t)e;
-      my[0][lane] = __ldg(r);
-      my[1][lane] = __ldg(r + 1);
-      if (LOSS) my[2][lane] = __ldg(r + 2);
-      my[3][lane] = __ldg(r + 3);
+      stage_record<LOSS>(my, lane, rec + 4 * (int64_t)e);
       my_e[lane] = e;
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncwarp();
     // One visit: the splat's gradient at this lane's pixel, stored as 16 rows
     // of the reduction scratch.  Branch-free: every lane evaluates the splat;
