@@ -307,28 +307,35 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
 }
 
 // Warp reduction of the gradient slots of one or two records.  First lanes l
-// and l^16 fold their 16 values with shuffles: the lower lane keeps slots 0-7,
-// the upper one slots 8-15, each summed over both lanes.  The 8 values then go
-// to the warp's shared scratch as rows red[row][lane] (rows 0-7: record A,
-// 8-15: record B; stride kRedStride = 36 floats keeps the row stores and the
-// 16-byte loads free of bank conflicts), and lane l adds the half row holding
-// slot l & 15 of record l >> 4 with four 16-byte loads.  The shuffle fold
-// halves the shared-memory traffic of a transpose through shared memory.
+// and l^16 fold their 16 values with shuffles: in each of four pairs of
+// float2 slots the lower lane keeps one (P_k) and the upper lane the other
+// (Q_k), each summed over both lanes; every lane computes the half it keeps
+// and the half it sends, choosing them by its half of the warp as cheaply as
+// the slot's form allows.  The 8 kept values then go to the warp's shared
+// scratch as rows red[row][lane] (rows 0-7: record A, 8-15: record B; stride
+// kRedStride = 36 floats keeps the row stores and the 16-byte loads free of
+// bank conflicts), and lane l adds the half row holding value l & 15 of record
+// l >> 4 with four 16-byte loads: P_k (k = (l & 7) >> 1) for l & 15 < 8, else
+// Q_k.  The shuffle fold halves the shared-memory traffic of a transpose
+// through shared memory.
 constexpr int kRedStride = 36;
 
-__device__ inline void fold_store(const float2 (&g)[8], float* __restrict__ rows) {
+__device__ inline void fold_store(const float2 (&keep)[4], const float2 (&send)[4], float* __restrict__ rows) {
   const int lane = threadIdx.x & 31;
-  const bool hi = lane & 16;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float2 send = hi ? g[k] : g[k + 4];
-    const float2 keep = hi ? g[k + 4] : g[k];
-    const float2 recv = make_float2(__shfl_xor_sync(kFull, send.x, 16), __shfl_xor_sync(kFull, send.y, 16));
-    const float2 h = __fadd2_rn(keep, recv);
+    const float2 recv = make_float2(__shfl_xor_sync(kFull, send[k].x, 16), __shfl_xor_sync(kFull, send[k].y, 16));
+    const float2 h = __fadd2_rn(keep[k], recv);
     rows[(2 * k) * kRedStride + lane] = h.x;
     rows[(2 * k + 1) * kRedStride + lane] = h.y;
   }
 }
+
+// The record slot that reduced value s = lane & 15 adds to (4 bits per value):
+// P0 = gs d -> (U, V); P1 = w (dC0, dC1) -> (R, G); P2 = (gs dy^2, gs) -> (CC, O);
+// P3 = sd d -> (P0, P1); Q0 = gs dx d -> (CA, CB); Q1 = w (dC2, dN0) -> (B, N0);
+// Q2 = (0, sd) -> (CUT, Z); Q3 = w (dN1, dN2) -> (N1, N2).
+constexpr unsigned long long kFoldSlots = 0xba76fe329854dc10ull;
 
 __device__ inline float reduce_rows(const float* __restrict__ red) {
   const int lane = threadIdx.x & 31, s = lane & 15;
@@ -402,6 +409,10 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
   // running "behind" sums of (r, g, b, n0, n1, n2) and the upstream of the same six, as pairs
   float2 S01 = make_float2(0.f, 0.f), S23 = make_float2(0.f, 0.f), S45 = make_float2(0.f, 0.f);
   const float2 U01 = make_float2(dC[0], dC[1]), U23 = make_float2(dC[2], dN[0]), U45 = make_float2(dN[1], dN[2]);
+  // the fold's pairs: lanes 0-15 keep P_k, lanes 16-31 Q_k (kFoldSlots)
+  const bool hi = lane & 16;
+  const float2 Ukeep = hi ? U23 : U01, Usend = hi ? U01 : U23;
+  const int slot = (int)((kFoldSlots >> (4 * (lane & 15))) & 15u);
   const float2 nfp = make_float2(-fpx, -fpy);
   // the forward's per-chunk masks name the records some lane of this block
   // blended; the others have zero gradient here and are not replayed
@@ -429,8 +440,9 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       // first seven hold sums that are linear in the splat's conic, p and o:
       // (S gs dx, S gs dy) (S gs dx^2, S gs dx dy) (S gs dy^2, S gs) (0, S sd)
       // (S sd dx, S sd dy), with gs = dL/dsigma and sd = dL/dd; the preprocess
-      // backward applies the constants once per entry
-      float2 gr[8];
+      // backward applies the constants once per entry.  They are folded in the
+      // pairs (P_k, Q_k) of kFoldSlots: this lane keeps one half, sends the other
+      float2 keep[4], send[4];
       const bool live = idx <= last;
       // the depth plane (p, z) only for Eq. 23
       const float4 a = my[0][j], b = my[1][j], e3 = my[3][j];
@@ -450,9 +462,8 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float2 w2 = make_float2(w, w);
       // colour and normal: (rgb, n) and the upstream (dC, dN) as three pairs
       const float2 x0 = make_float2(e3.x, e3.y), x1 = make_float2(e3.z, e3.w), x2 = make_float2(b.z, b.w);
-      gr[5] = __fmul2_rn(w2, U45);
-      gr[6] = __fmul2_rn(w2, U01);
-      gr[7] = __fmul2_rn(w2, U23);
+      keep[1] = __fmul2_rn(w2, Ukeep);   // w (dC0, dC1) | w (dC2, dN0)
+      send[1] = __fmul2_rn(w2, Usend);
       // (x - S) enters both dL/dalpha and the update S += alpha (x - S)
       const float2 q0 = __fadd2_rn(x0, make_float2(-S01.x, -S01.y));
       const float2 q1 = __fadd2_rn(x1, make_float2(-S23.x, -S23.y));
@@ -468,16 +479,19 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       // d = z_c + p . Delta (Eq. 4): the median splat, and Eq. 23 with the weights constant
       float sd = (contrib && idx == med) ? dD : 0.f;
       if (LOSS) sd += c4 * w * ((e2.z + e2.x * dx + e2.y * dy) - dmean);
-      gr[3] = make_float2(0.f, sd);
-      gr[4] = __fmul2_rn(make_float2(sd, sd), d);
+      const float2 p3 = __fmul2_rn(make_float2(sd, sd), d), q3 = __fmul2_rn(w2, U45);
+      keep[3] = hi ? q3 : p3;            // sd d | w (dN1, dN2)
+      send[3] = hi ? p3 : q3;
       // alpha = o G below the clamp: dL/dsigma = -dL/dalpha alpha
       const float gs = raw <= amax ? -dal * al : 0.f;
-      const float2 gs2 = make_float2(gs, gs);
-      gr[0] = __fmul2_rn(gs2, d);
-      const float2 gq = __fmul2_rn(gs2, d2);
-      gr[1] = make_float2(gq.x, gr[0].x * dy);
-      gr[2] = make_float2(gq.y, gs);
-      fold_store(gr, rows);
+      const float gsx = gs * dx;
+      const float sk = hi ? gsx : gs, ss = hi ? gs : gsx;
+      keep[0] = __fmul2_rn(make_float2(sk, sk), d);   // gs d | gs dx d
+      send[0] = __fmul2_rn(make_float2(ss, ss), d);
+      const float gy2 = gs * d2.y;
+      keep[2] = make_float2(hi ? 0.f : gy2, hi ? sd : gs);   // (gs dy^2, gs) | (0, sd)
+      send[2] = make_float2(hi ? gy2 : 0.f, hi ? gs : sd);
+      fold_store(keep, send, rows);
     };
     // some lane blends every replayed record (the forward's mask), so every
     // visit reduces.  Records go back to front, two per round where possible:
@@ -500,7 +514,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       __syncwarp();
       const float s = reduce_rows(my_red);   // lanes 16-31 read stale rows without jB
       __syncwarp();   // the scratch is rewritten by the next round
-      const int slot = lane & 15, j = lane < 16 ? jA : jB;
+      const int j = lane < 16 ? jA : jB;
       if (j >= 0 && slot != G_UNUSED && s != 0.f) atomicAdd(grad + (int64_t)my_e[j] * kRecFloats + slot, s);
     }
     __syncwarp();
