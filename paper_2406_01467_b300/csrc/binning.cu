@@ -40,7 +40,9 @@ __device__ inline void hist_keys(uint32_t (*h)[kRadix], int passes, uint32_t key
   const unsigned vm = __ballot_sync(FULL, valid);
   if (vm == 0) return;
   const int leader = __ffs(vm) - 1;
-  for (int p = 0; p < passes; ++p) {
+#pragma unroll
+  for (int p = 0; p < kMaxPasses; ++p) {
+    if (p >= passes) break;
     const int d = (int)((key >> (kRadixBits * p)) & (kRadix - 1));
     if (p < tested) {
       if (valid) atomicAdd(&h[p][d], 1u);

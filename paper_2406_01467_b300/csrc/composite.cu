@@ -138,13 +138,13 @@ __device__ inline SubRect sub_rect(int x0, int y0, int sub_per_row, int sub) {
 }
 
 // Can the splat (first two record float4s) reach any pixel of the rectangle?
-// s_cut = log2(o / alpha_min): beyond it alpha < alpha_min, with a margin
+// s_cut = log2(o) - log2(alpha_min) (lg_amin): beyond it alpha < alpha_min, with a margin
 // (1e-4 relative, 1.5e-4 absolute) far above the error of the FP32 operations
 // and of __log2f, so the test only ever skips splats the alpha test rejects at
 // every pixel.
-__device__ inline bool reaches(const float4& f0, const float4& f1, const SubRect& R, float amin) {
+__device__ inline bool reaches(const float4& f0, const float4& f1, const SubRect& R, float lg_amin) {
   const float ia = __fdividef(0.5f, f0.z), ic = __fdividef(0.5f, f1.x);
-  const float cut = __log2f(__fdividef(f1.y, amin)) * 1.0001f + 1.5e-4f;
+  const float cut = (__log2f(f1.y) - lg_amin) * 1.0001f + 1.5e-4f;
   return rect_min_sigma(f0.x, f0.y, f0.z, f0.w, f1.x, ia, ic, R.X0, R.X1, R.Y0, R.Y1) <= cut;
 }
 
@@ -186,6 +186,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   const uint32_t* pval = at<uint32_t>(ws, L.pval_final);
   const float4* rec = at<float4>(ws, L.rec);
   const float amin = fd->alpha_min, amax = fd->alpha_max, tmin = fd->T_min, tmed = fd->median_T;
+  const float lg_amin = __log2f(amin);
   const float fpx = c.px + 0.5f, fpy = c.py + 0.5f;
   const float2 nfp = make_float2(-fpx, -fpy);
   const int lane = threadIdx.x & 31;
@@ -215,7 +216,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
     cp_async_wait<1>();     // this lane's copies of chunk c0 have landed
     __syncwarp();           // ... and every lane's are visible
     float4 (*my)[32] = buf[cur];
-    const bool rel = c0 + lane < range.y && reaches(my[0][lane], my[1][lane], R, amin);
+    const bool rel = c0 + lane < range.y && reaches(my[0][lane], my[1][lane], R, lg_amin);
     unsigned m = __ballot_sync(kFull, rel);
     uint32_t cm = 0;        // records of the chunk this lane blends
     while (m) {
