@@ -103,21 +103,22 @@ __device__ inline float ex2(float x) {
 }
 
 // Minimum of sigma over the rectangle [X0, X1] x [Y0, Y1] (pixel-centre
-// coordinates): zero if the centre is inside.  Otherwise the minimum lies on
-// an edge facing the centre: sigma grows along the segment from the centre to
-// any point of the rectangle (it scales with the square of the distance along
-// it), and that segment enters the rectangle through an edge whose outside
-// holds the centre.  So one vertical and one horizontal edge suffice (the
-// facing one where there is one; either edge otherwise, which only adds a
-// candidate), each a 1D convex quadratic clamped to the edge.
+// coordinates).  It lies on an edge facing the centre, if the centre is
+// outside: sigma grows along the segment from the centre to any point of the
+// rectangle (it scales with the square of the distance along it), and that
+// segment enters the rectangle through an edge whose outside holds the centre.
+// So two candidates suffice, each a 1D convex quadratic minimised along a
+// line and clamped to the rectangle: x = u clamped to [X0, X1] (the facing
+// vertical edge, or the centre's own column), and y = v clamped likewise.
+// Both are points of the rectangle, and with the centre inside the first is
+// the centre itself (sigma 0).
 __device__ inline float rect_min_sigma(float u, float v, float a, float b, float c, float ia,
                                        float ic, float X0, float X1, float Y0, float Y1) {
-  if (u >= X0 && u <= X1 && v >= Y0 && v <= Y1) return 0.f;
-  // vertical edge x = X: dx fixed, dy minimises 2 c dy + b dx = 0 (ic = 1 / 2c)
-  const float dx = u - (u < X0 ? X0 : X1);
+  // x fixed: dy minimises 2 c dy + b dx = 0 (ic = 1 / 2c)
+  const float dx = u - fminf(fmaxf(u, X0), X1);
   const float y = fminf(fmaxf(v + b * dx * ic, Y0), Y1);
-  // horizontal edge y = Y
-  const float dy = v - (v < Y0 ? Y0 : Y1);
+  // y fixed
+  const float dy = v - fminf(fmaxf(v, Y0), Y1);
   const float x = fminf(fmaxf(u + b * dy * ia, X0), X1);
   return fminf(quad(a, b, c, dx, v - y), quad(a, b, c, u - x, dy));
 }
