@@ -472,9 +472,19 @@ __global__ void __launch_bounds__(1024) k_tile_order(const int2* __restrict__ ra
     atomicAdd(&cnt[cost_bucket(c)], 1);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {   // exclusive offsets, heaviest bucket first
-    int acc = 0;
-    for (int b = 255; b >= 0; --b) { const int n = cnt[b]; cnt[b] = acc; acc += n; }
+  if (threadIdx.x < 32) {   // exclusive offsets, heaviest bucket first: lane l owns buckets 255-8l .. 248-8l
+    const int lane = threadIdx.x;
+    int n[8], sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { n[i] = cnt[255 - 8 * lane - i]; sum += n[i]; }
+    int incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int acc = incl - sum;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { cnt[255 - 8 * lane - i] = acc; acc += n[i]; }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < T; t += blockDim.x) {
