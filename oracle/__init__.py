@@ -30,4 +30,4 @@ finite differences) by the ``-m "not gpu"`` tests.
 """
 from .params import RenderParams  # noqa: F401
 from . import sh, gaussians, binning, composite, losses, filter3d, appearance  # noqa: F401
-from .render import render, render_grads  # noqa: F401
+from .render import evaluated_in, fp32_spread, render, render_grads  # noqa: F401

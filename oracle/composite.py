@@ -97,8 +97,8 @@ def composite(pre, dec, width, height, params: RenderParams, pixels=None):
     gsafe = torch.from_numpy(np.where(valid, gidx, pad))
     vmask = torch.from_numpy(valid)
 
-    px = torch.from_numpy((pixels % width).astype(np.float64) + 0.5)
-    py = torch.from_numpy((pixels // width).astype(np.float64) + 0.5)
+    px = torch.from_numpy((pixels % width).astype(np.float64) + 0.5).to(DT)
+    py = torch.from_numpy((pixels // width).astype(np.float64) + 0.5).to(DT)
 
     u = pre["u"][gsafe]
     v = pre["v"][gsafe]

@@ -110,7 +110,7 @@ def render_with_losses(scene, cam, upstream=None, params: RenderParams = None):
                 weights=r["weights"], d_all=r["d_all"])
     if upstream is None:
         return {k: (v.detach().numpy() if torch.is_tensor(v) else v) for k, v in maps.items()}, None, None
-    dC, dA, dD, dN, dLd, dLn = [torch.from_numpy(np.asarray(x, np.float64)) for x in upstream]
+    dC, dA, dD, dN, dLd, dLn = [torch.from_numpy(np.asarray(x, np.float64)).to(DT) for x in upstream]
     loss = ((r["color"] * dC.reshape(3, -1).T).sum() + (r["alpha"] * dA.reshape(-1)).sum()
             + (r["depth"] * dD.reshape(-1)).sum() + (r["normal"] * dN.reshape(3, -1).T).sum()
             + (Ld * dLd.reshape(-1)).sum() + (Ln * dLn.reshape(-1)).sum())

@@ -1,6 +1,9 @@
 """Oracle entry points: forward maps and FP64 gradients for one camera."""
 from __future__ import annotations
 
+import contextlib
+import sys
+
 import numpy as np
 import torch
 
@@ -10,6 +13,59 @@ from .params import RenderParams
 DT = torch.float64
 PARAM_NAMES = ("means", "scales", "quats", "opacities", "sh")
 PRE2D = ("u", "v", "conic", "opacity", "rgb", "n", "z", "p")
+
+
+@contextlib.contextmanager
+def evaluated_in(dtype):
+    """Runs the oracle's floating-point arithmetic in ``dtype`` instead of FP64.
+
+    A test instrument only: the FP64 results are the reference.  The same
+    definition evaluated in FP32 shows how far FP32 rounding alone moves each
+    result, which is the scale against which an FP32 implementation's
+    differences from the FP64 values are judged entry by entry.  The binning
+    decisions are FP32 either way."""
+    from . import appearance, losses
+    mods = (gaussians, comp, losses, appearance, sys.modules[__name__])
+    old = [m.DT for m in mods]
+    try:
+        for m in mods:
+            m.DT = dtype
+        yield
+    finally:
+        for m, d in zip(mods, old):
+            m.DT = d
+
+
+def fp32_spread(grad_fn, scene, samples=4, seed=0):
+    """FP64 gradients and, entry by entry, how far FP32 evaluations move them.
+
+    A test instrument (no counterpart in the paper).  ``grad_fn(scene)`` returns
+    a dict of gradient arrays computed by the oracle.  It is evaluated once in
+    FP64 (the reference) and ``samples`` times in FP32: at the scene's own
+    parameters, then at parameters each moved by -1, 0 or +1 unit in the last
+    place of FP32, at random.  Returns (ref, spread), spread holding the
+    largest |FP32 - FP64| of each entry over the samples: the amount by which
+    rounding to FP32 inside the computation, or a one-ulp change of an input,
+    moves that entry.  It is large only where the entry is ill-conditioned
+    (terms that cancel over the pixels, thin splats whose conic inverts a
+    nearly singular 2x2 matrix), and an FP32 implementation cannot be asked to
+    match the FP64 value more closely than a small multiple of it."""
+    ref = {k: np.asarray(v, np.float64) for k, v in grad_fn(scene).items()}
+    spread = {k: np.zeros_like(v) for k, v in ref.items()}
+    rng = np.random.default_rng(seed)
+    for s in range(samples):
+        sc = scene
+        if s > 0:
+            moved = {}
+            for k in PARAM_NAMES:
+                a = np.ascontiguousarray(getattr(scene, k), np.float32)
+                moved[k] = (a.view(np.int32) + rng.integers(-1, 2, a.shape).astype(np.int32)).view(np.float32)
+            sc = type(scene)(**{**scene.__dict__, **moved})
+        with evaluated_in(torch.float32):
+            g = grad_fn(sc)
+        for k in ref:
+            spread[k] = np.maximum(spread[k], np.abs(np.asarray(g[k], np.float64) - ref[k]))
+    return ref, spread
 
 
 def _leaves(scene, requires_grad):
@@ -91,10 +147,9 @@ def render_grads(scene, cam, upstream, params: RenderParams = None, pixels=None,
     maps = {k: [] for k in ("color", "alpha", "depth", "normal", "margin")}
     for px in _chunks(pixels, chunk):
         r = comp.composite(pre_d, dec, W_, H_, params, px)
-        loss = ((r["color"] * torch.from_numpy(dC[:, px].T)).sum()
-                + (r["alpha"] * torch.from_numpy(dA[px])).sum()
-                + (r["depth"] * torch.from_numpy(dD[px])).sum()
-                + (r["normal"] * torch.from_numpy(dN[:, px].T)).sum())
+        t = lambda a: torch.from_numpy(a).to(DT)
+        loss = ((r["color"] * t(dC[:, px].T)).sum() + (r["alpha"] * t(dA[px])).sum()
+                + (r["depth"] * t(dD[px])).sum() + (r["normal"] * t(dN[:, px].T)).sum())
         gs = torch.autograd.grad(loss, [pre_d[k] for k in PRE2D], allow_unused=True)
         for k, gk in zip(PRE2D, gs):
             if gk is not None:
@@ -112,3 +167,4 @@ def render_grads(scene, cam, upstream, params: RenderParams = None, pixels=None,
     maps["pixels"] = pixels
     maps["dec"] = dec
     return param_grads, grads2d, maps
+
