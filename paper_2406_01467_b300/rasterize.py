@@ -318,12 +318,17 @@ class Frame:
 
 
 class _Rasterize(torch.autograd.Function):
+    """Differentiable single-view render (Eq. 3, Eq. 4 with the plane of Eq. 13-17,
+    Eq. 22): forward = gs_preprocess + gs_bin + gs_render_fwd, backward =
+    gs_render_bwd, which replays each pixel's compositing instead of storing
+    per-(pixel, splat) state."""
+
     @staticmethod
-    def forward(ctx, means, scales, quats, opacities, sh, state):
-        frame: Frame = state["frame"]
-        frame.forward()
+    def forward(ctx, means, scales, quats, opacities, sh, frame, sync):
+        frame.forward(sync_capacity=sync)
         ctx.frame = frame
         ctx.dtype = means.dtype
+        ctx.set_materialize_grads(False)   # unused maps reach the library as NULL (zero)
         c, a, d, n = frame.view_maps(0)
         return c.clone(), a.clone(), d.clone(), n.clone()
 
@@ -331,18 +336,39 @@ class _Rasterize(torch.autograd.Function):
     def backward(ctx, dc, da, dd, dn):
         frame: Frame = ctx.frame
         g = frame.backward(dc, da, dd, dn)[0]
-        cast = lambda t: t.to(ctx.dtype)
+        cast = lambda t: t if t.dtype == ctx.dtype else t.to(ctx.dtype)
         return (cast(g["means"]), cast(g["scales"]), cast(g["quats"]), cast(g["opacities"]),
-                cast(g["sh"]), None)
+                cast(g["sh"]), None, None)
 
 
 def rasterize(means, scales, quats, opacities, sh, camera, sh_degree: int,
-              params: RenderParams = None, pair_capacity: Optional[int] = None):
+              params: RenderParams = None, pair_capacity: Optional[int] = None,
+              frame: Optional[Frame] = None, sync: Optional[bool] = None):
     """Render one view; differentiable w.r.t. all five parameter tensors.
 
-    Returns (colour [3,H,W], alpha [H,W], depth [H,W], normal [3,H,W])."""
+    Returns (colour [3,H,W], alpha [H,W], depth [H,W], normal [3,H,W]); their
+    gradients flow to means, scales, quats, opacities and sh (FP32 or BF16, all
+    the same dtype), including through the planar depth and the normal.
+
+    ``frame`` reuses the workspace of an earlier call (a Frame of one view whose
+    scene has the same size; it is pointed at the new tensors), so a training
+    loop allocates nothing per step.  A frame serves one pending backward at a
+    time: render, backward, then render again.
+
+    ``sync`` (default: True unless ``pair_capacity`` is given) checks the pair
+    count on the host after binning and grows the workspace if needed.  With
+    False nothing synchronises, so the call can be captured in a CUDA graph; a
+    frame whose pairs exceed the capacity then leaves its maps and gradients
+    unwritten and reports GS_ERR_CAPACITY through ``frame.stats()``."""
     st = SceneTensors(means.detach().contiguous(), scales.detach().contiguous(),
                       quats.detach().contiguous(), opacities.detach().contiguous(),
                       sh.detach().contiguous(), sh_degree)
-    frame = Frame([st], [(camera, 0)], params, pair_capacity)
-    return _Rasterize.apply(means, scales, quats, opacities, sh, {"frame": frame})
+    if frame is None:
+        frame = Frame([st], [(camera, 0)], params, pair_capacity)
+    else:
+        if len(frame.views) != 1 or len(frame.scenes) != 1:
+            raise ValueError("rasterize renders one view of one scene")
+        frame.rebind([st])
+    if sync is None:
+        sync = pair_capacity is None
+    return _Rasterize.apply(means, scales, quats, opacities, sh, frame, bool(sync))

@@ -76,3 +76,73 @@ def grad2d_to_record(g2d, pre):
         "n": M[:, [15, 10, 11]],
         "rgb": M[:, 12:15],
     }
+
+
+# Gradients, entry by entry: |gpu - ref| <= GRAD_REL |ref| + GRAD_SPREAD spread
+# + GRAD_FLOOR max|ref|, where ref is the FP64 oracle and spread the largest
+# change of that entry over FP32 evaluations of the oracle (oracle.fp32_spread).
+# The relative 1e-3 alone is out of reach of any FP32 evaluation on the entries
+# that are sums of cancelling terms or that pass through a nearly singular
+# conic: the oracle's own FP32 evaluation misses it on about 1% of them.
+GRAD_REL = 1e-3
+GRAD_SPREAD = 16.0
+GRAD_FLOOR = 1e-9
+
+
+def grad_report(g_gpu, g_ref, spread=None, rel=GRAD_REL, c_spread=GRAD_SPREAD, floor=GRAD_FLOOR):
+    """Per-entry comparison of gradient arrays (dicts of arrays).
+
+    Returns {name: dict(n, bad, worst, worst_index, worst_ref, norm)}: ``bad``
+    entries miss the bound above (without ``spread``: |gpu - ref| <= rel |ref|
+    on entries above 1e-6 of the largest); ``worst`` is the largest ratio of an
+    entry's difference to its bound; ``norm`` = ||gpu - ref|| / ||ref||."""
+    out = {}
+    for k in g_ref:
+        a = np.asarray(g_gpu[k], np.float64).reshape(-1)
+        b = np.asarray(g_ref[k], np.float64).reshape(-1)
+        assert a.shape == b.shape, (k, a.shape, b.shape)
+        scale = np.abs(b).max(initial=0.0)
+        err = np.abs(a - b)
+        if spread is None:
+            sel = np.abs(b) > 1e-6 * scale
+            bound = np.where(sel, rel * np.abs(b), np.inf)
+        else:
+            bound = rel * np.abs(b) + c_spread * np.asarray(spread[k], np.float64).reshape(-1) + floor * scale
+        r = err / np.where(bound > 0, bound, 1e-300)
+        i = int(np.argmax(r)) if len(r) else 0
+        out[k] = dict(n=int(np.isfinite(bound).sum()), bad=int((err > bound).sum()),
+                      worst=float(r[i]) if len(r) else 0.0, worst_index=i,
+                      worst_ref=float(b[i]) if len(b) else 0.0,
+                      norm=float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)))
+    return out
+
+
+def assert_grads_close(g_gpu, g_ref, spread=None, what="", **kw):
+    """Fails unless every entry of every array is within its bound (grad_report)
+    and each array's relative norm error is within GRAD_REL."""
+    rep = grad_report(g_gpu, g_ref, spread, **kw)
+    bad = {k: v for k, v in rep.items() if v["bad"] or v["norm"] > kw.get("rel", GRAD_REL)}
+    assert not bad, f"{what}: {bad}"
+    assert any(v["n"] for v in rep.values()), f"{what}: nothing to compare"
+    return rep
+
+
+def oracle_grads_with_spread(scene, cam, up, op, pixels=None, fn=None):
+    """FP64 oracle gradients of the parameters and of the 2D quantities for the
+    upstream maps ``up``, and their FP32 spreads (oracle.fp32_spread).
+    Returns (param_grads, grads2d, param_spread, grads2d_spread).  ``fn(scene)``
+    replaces oracle.render_grads (it must return the same first two items)."""
+    import oracle
+
+    def grads(s):
+        pg, g2 = (fn(s) if fn else oracle.render_grads(s, cam, up, op, pixels=pixels))[:2]
+        return {**pg, **{"2d." + k: v for k, v in g2.items()}}
+
+    ref, spread = oracle.fp32_spread(grads, scene)
+
+    def split(d):
+        return ({k: v for k, v in d.items() if not k.startswith("2d.")},
+                {k[3:]: v for k, v in d.items() if k.startswith("2d.")})
+
+    (pg, g2), (sp, s2) = split(ref), split(spread)
+    return pg, g2, sp, s2

@@ -5,6 +5,8 @@ import numpy as np
 import pytest
 import torch
 
+from tests._util import assert_grads_close
+
 from oracle import appearance as oapp
 from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, scenes
 from paper_2406_01467_b300.appearance import Appearance, adam_step
@@ -64,9 +66,7 @@ def test_one_call_matches_oracle():
         ok = m.all(axis=0)[None].repeat(3, 0)
         # terms of size 1/(3HW) cancel: absolute tolerance on that scale
         np.testing.assert_allclose(a[ok], b[ok], rtol=1e-5, atol=1e-5 * np.abs(b).max())
-    g = app.grads.cpu().numpy()
-    s = np.abs(g_ref).max()
-    assert np.abs(g - g_ref).max() <= 1e-3 * s, np.abs(g - g_ref).max() / s
+    assert_grads_close({"params": app.grads.cpu().numpy()}, {"params": g_ref}, what="appearance gradients")
 
 
 def test_adam_matches_oracle():

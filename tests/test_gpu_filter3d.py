@@ -7,7 +7,7 @@ import torch
 import oracle
 from oracle import binning, filter3d
 from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, scenes
-from tests._util import AMBIG_MARGIN, _same_ranges, compare_maps, gpu_maps_at, oracle_params
+from tests._util import assert_grads_close, oracle_grads_with_spread, AMBIG_MARGIN, _same_ranges, compare_maps, gpu_maps_at, oracle_params
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
@@ -90,11 +90,7 @@ def test_filtered_maps_and_gradients_match_oracle():
     amb = (ref["margin"] < AMBIG_MARGIN).reshape(cam.height, cam.width)
     up = [u[0] for u in scenes.upstream_grads(9, cam.height, cam.width)]
     up = [np.where(amb if u.ndim == 2 else amb[None], 0.0, u).astype(np.float32) for u in up]
-    pg, _, _ = oracle.render_grads(sc, cam, up, op)
+    pg, _, sp, _ = oracle_grads_with_spread(sc, cam, up, op)
     g = fr.backward(*[torch.from_numpy(u).to(DEV) for u in up])[0]
     torch.cuda.synchronize()
-    for k in pg:
-        a, b = g[k].cpu().numpy().astype(np.float64), pg[k]
-        s = np.abs(b).max()
-        assert np.abs(a - b).max() <= 1e-3 * s, (k, np.abs(a - b).max() / s)
-        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b), k
+    assert_grads_close({k: v.cpu().numpy() for k, v in g.items()}, pg, sp, what="filtered gradients")

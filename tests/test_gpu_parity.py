@@ -2,8 +2,8 @@
 
 Tile lists and sort order: bit-exact.  Colour, alpha, normal: 1e-4 absolute;
 depth: 1e-4 relative, on pixels whose discrete decisions are not within the
-FP32/FP64 ambiguity margin.  Gradients: relative 1e-3 of each parameter
-group's scale.
+FP32/FP64 ambiguity margin.  Gradients: every entry within 1e-3 relative plus
+16 times the change FP32 evaluations of the oracle make to it (tests/_util.py).
 """
 import numpy as np
 import pytest
@@ -12,7 +12,8 @@ import torch
 import oracle
 from oracle import binning
 from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, scenes
-from tests._util import _same_ranges, AMBIG_MARGIN, compare_maps, gpu_maps_at, grad2d_to_record, oracle_params
+from tests._util import (_same_ranges, AMBIG_MARGIN, assert_grads_close, compare_maps, gpu_maps_at,
+                         grad2d_to_record, oracle_grads_with_spread, oracle_params)
 
 pytestmark = pytest.mark.gpu
 
@@ -92,18 +93,6 @@ def test_forward_is_tile_size_independent():
             np.testing.assert_array_equal(a, b)
 
 
-def _grad_compare(g_gpu, g_ref, rel=1e-3):
-    """Per-array check: |gpu - ref| <= rel * max|ref| elementwise, plus a norm check."""
-    out = {}
-    for k in g_ref:
-        a = np.asarray(g_gpu[k], np.float64)
-        b = np.asarray(g_ref[k], np.float64)
-        scale = np.abs(b).max()
-        err = np.abs(a - b).max()
-        out[k] = (err / max(scale, 1e-30), np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-    return out
-
-
 def _upstream(cam, seed, ambiguous_mask=None):
     up = [u[0] for u in scenes.upstream_grads(seed, cam.height, cam.width)]
     if ambiguous_mask is not None:
@@ -123,7 +112,7 @@ def test_backward_matches_oracle_tiny(tile):
     ref_f = oracle.render(sc, cam, op)
     amb = ref_f["margin"] < AMBIG_MARGIN
     up = _upstream(cam, 7, amb)
-    pg, g2, _ = oracle.render_grads(sc, cam, up, op)
+    pg, g2, sp, s2 = oracle_grads_with_spread(sc, cam, up, op)
     fr = _frame(sc, cam, p)
     ups = [torch.from_numpy(u).to(DEV) for u in up]
     grads = fr.backward(*ups)[0]
@@ -134,10 +123,88 @@ def test_backward_matches_oracle_tiny(tile):
     rec = grad2d_to_record(dbg[v], {k: ref_f["pre"][k][v] for k in ("conic", "p", "opacity")})
     g2_gpu = {k: rec[k].reshape(g2[k][v].shape) for k in rec}
     g2_ref = {k: g2[k][v] for k in rec}
-    rep2 = _grad_compare(g2_gpu, g2_ref)
-    for k, (emax, enorm) in rep2.items():
-        assert emax < 1e-3 and enorm < 1e-3, (k, rep2)
+    assert_grads_close(g2_gpu, g2_ref, {k: s2[k][v] for k in rec}, what="2D gradients")
     gpu = {k: g.cpu().numpy() for k, g in grads.items()}
-    rep = _grad_compare(gpu, pg)
-    for k, (emax, enorm) in rep.items():
-        assert emax < 1e-3 and enorm < 1e-3, (k, rep)
+    assert_grads_close(gpu, pg, sp, what="parameter gradients")
+
+
+def _clamp_scene():
+    """The tiny scene plus large splats centred beyond each border of the image
+    widened by the J clamp's margin (and beyond two corners), whose footprints
+    still reach the image: their J rows are clamped (3D GS default, Sec. 4.1.1)."""
+    sc = scenes.tiny_scene(600, seed=11)
+    z = np.array([3.0, 3.5, 2.5, 4.0, 3.2, 2.8], np.float32)
+    txy = np.array([[1.2, 0.1], [-1.15, -0.2], [0.2, 1.1], [-0.1, -0.95], [1.1, 1.05], [-1.1, 1.2]], np.float32)
+    means = np.c_[txy * z[:, None], z].astype(np.float32)
+    rng = np.random.default_rng(12)
+    big = scenes.Scene(means, rng.uniform(0.5, 0.9, (6, 3)).astype(np.float32),
+                       rng.standard_normal((6, 4)).astype(np.float32),
+                       rng.uniform(0.5, 0.95, 6).astype(np.float32),
+                       rng.normal(0, 0.3, (6, 1, 3)).astype(np.float32), 0)
+    cat = lambda a, b: np.concatenate([a, b]).astype(np.float32)
+    return scenes.Scene(cat(sc.means, big.means), cat(sc.scales, big.scales), cat(sc.quats, big.quats),
+                        cat(sc.opacities, big.opacities), cat(sc.sh, big.sh), 0), 6
+
+
+def test_clamped_jacobian_splats_match_oracle():
+    # splats whose J clamps: maps over the whole image and per-entry gradients
+    sc, n_big = _clamp_scene()
+    cam = scenes.tiny_camera()
+    p = RenderParams()
+    op = oracle_params(p)
+    ref_f = oracle.render(sc, cam, op)
+    from oracle.params import clamp_limits_f32
+    lims = clamp_limits_f32(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, op.clamp_margin)
+    tx = (ref_f["pre"]["u"] - cam.cx) / cam.fx
+    ty = (ref_f["pre"]["v"] - cam.cy) / cam.fy
+    clamped = (tx < lims[0]) | (tx > lims[1]) | (ty < lims[2]) | (ty > lims[3])
+    assert (clamped & ref_f["dec"]["valid"])[-n_big:].all()
+    fr = _frame(sc, cam, p)
+    pixels = np.arange(cam.width * cam.height)
+    bad, rep = compare_maps(gpu_maps_at(fr, pixels), ref_f, ref_f["margin"])
+    assert rep["ambiguous"] < 1e-2 and rep["n_bad"] == 0, rep
+    # the big splats decide what the border pixels show
+    a_big = oracle.render(sc.subset(np.arange(sc.n - n_big, sc.n)), cam, op)["alpha"]
+    assert (a_big > 0.05).mean() > 0.1
+    up = _upstream(cam, 8, ref_f["margin"] < AMBIG_MARGIN)
+    pg, _, sp, _ = oracle_grads_with_spread(sc, cam, up, op)
+    grads = fr.backward(*[torch.from_numpy(u).to(DEV) for u in up])[0]
+    torch.cuda.synchronize()
+    gpu = {k: g.cpu().numpy() for k, g in grads.items()}
+    assert_grads_close(gpu, pg, sp, what="parameter gradients")
+    # the clamped splats' own gradients, at the strict relative bound where FP32 can meet it
+    big = {k: v[-n_big:] for k, v in gpu.items()}
+    assert_grads_close(big, {k: v[-n_big:] for k, v in pg.items()}, {k: v[-n_big:] for k, v in sp.items()},
+                       what="clamped splats' gradients")
+    assert all(np.abs(pg[k][-n_big:]).max() > 0 for k in pg)
+
+
+def test_backward_run_to_run_differences_are_bounded():
+    # The compositing backward adds each visit's per-splat sums to the entry's
+    # 2D-gradient slots with FP32 atomics, so the order of those additions, and
+    # with it the last bits of a gradient, changes from run to run (the
+    # per-visit partial sums themselves are computed the same way every time).
+    # Stated bound: two runs differ, entry by entry, by at most 8 times the
+    # FP32 spread of that entry (measured: at most 3.1 times on this scene,
+    # under 1 on crops of the 3M scene); the maps are bit-identical.
+    sc, cam = scenes.tiny_scene(), scenes.tiny_camera()
+    p = RenderParams()
+    op = oracle_params(p)
+    ref_f = oracle.render(sc, cam, op)
+    up = _upstream(cam, 7, ref_f["margin"] < AMBIG_MARGIN)
+    fr = _frame(sc, cam, p)
+    runs = []
+    for _ in range(4):
+        g = fr.backward(*[torch.from_numpy(u).to(DEV) for u in up])[0]
+        torch.cuda.synchronize()
+        runs.append({k: v.cpu().numpy() for k, v in g.items()})
+    pg, _, sp, _ = oracle_grads_with_spread(sc, cam, up, op)
+    same = 0
+    for r in runs[1:]:
+        assert_grads_close(r, runs[0], sp, rel=0.0, c_spread=8.0, what="run-to-run")
+        same += sum(int((r[k] == runs[0][k]).sum()) for k in r)
+    total = 3 * sum(v.size for v in runs[0].values())
+    assert same > 0.5 * total   # most entries come out bit-identical
+    fr2 = _frame(sc, cam, p)
+    for a, b in zip(fr.view_maps(0), fr2.view_maps(0)):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)
