@@ -34,7 +34,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ms per fwd+bwd frame (colour+depth+normal) at 3M Gaussians, 1297x840"
 PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}
-N_SM, FP32_LANES = 148, 128
+# The method's own operations per blended (pixel, splat) pair (counted in the
+# design notes, section 6): forward 22 FP32 operations (offset 2, quadratic
+# form 6, alpha and its clamp 2, alpha test 1, transmittance 2, stop test 1,
+# weight 1, colour 3, normal 3, median test 1) and one exp; backward 60 FP32
+# operations (alpha recomputed 10, transmittance recovered 2, weight 1,
+# colour/normal gradients 6, behind sums 12, dL/dalpha 8, dL/dsigma 1, the
+# conic/centre/depth sums 5, their reduction over the pixels 15) plus one exp
+# and one reciprocal.  An FMA counts once.
+OPS_FWD, OPS_BWD = 22, 60
+MUFU_FWD, MUFU_BWD = 1, 2
 
 CONFIGS = {
     "unbounded": dict(workload="unbounded scene, 3M Gaussians, SH deg 3, 1297x840, FP32, fwd+bwd",
@@ -78,6 +87,75 @@ def load_traffic(config):
         if digest(rec["source"]) == d["source_sha256_16"].get(rec["source"]):
             out[stage] = int(rec["bytes"])
     return out
+
+
+def load_counters(config):
+    """Per-launch shared-memory wavefronts of the compositing kernels from the
+    committed ncu summary, or {} where the kernel changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "composite_counters_unbounded_3M_1297x840.json")
+    if config != "unbounded" or not os.path.exists(p):
+        return {}
+    with open(p) as f:
+        d = json.load(f)
+    csrc = os.path.join(ROOT, "paper_2406_01467_b300", "csrc")
+    m = hashlib.sha256()
+    for fn in ("composite.cu", "gs_internal.cuh"):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            m.update(fh.read())
+    if m.hexdigest()[:16] != d.get("source_sha256_16"):
+        return {}
+    return d["per_launch"]
+
+
+def measure_unit_peaks(device, target_ms=15.0):
+    """Peak rates of the units the compositing kernels run on, measured now on
+    this GPU with gs_peak_probe (CUDA events, best of 3 launches of about
+    target_ms each): FP32 FMAs/s (scalar and packed FP32x2), ex2/s and
+    shared-memory bytes/s, with the SM clock sampled meanwhile."""
+    import ctypes
+    import torch
+    from paper_2406_01467_b300 import _lib
+    lib = _lib.load()
+    sink = torch.zeros(1, device=device)
+    stream = torch.cuda.current_stream().cuda_stream
+    kinds = (("ffma", _lib.GS_PEAK_FFMA), ("ffma2", _lib.GS_PEAK_FFMA2), ("ex2", _lib.GS_PEAK_EX2),
+             ("lds128", _lib.GS_PEAK_LDS128))
+    out = {}
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(torch.cuda.current_device())
+    with sampler:
+        for name, kind in kinds:
+            work = ctypes.c_int64(0)
+            iters = 16
+            while True:
+                a.record()
+                _lib.check(lib.gs_peak_probe(kind, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(work),
+                                             ctypes.c_void_p(stream)), "gs_peak_probe")
+                b.record()
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b)
+                if ms >= target_ms / 4 or iters >= (1 << 22):
+                    break
+                iters *= 4
+            iters = int(min(1 << 24, max(1, iters * target_ms / max(ms, 1e-3))))
+            best = None
+            for _ in range(3):
+                a.record()
+                lib.gs_peak_probe(kind, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(work),
+                                  ctypes.c_void_p(stream))
+                b.record()
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b)
+                best = ms if best is None else min(best, ms)
+            out[name] = work.value / (best * 1e-3)
+    clk = sampler.summary(None)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = clk["sm_mhz"]
+    per_clk = {k: round(v / (sms * mhz * 1e6), 2) for k, v in out.items()} if mhz else None
+    return {"ffma_per_s": out["ffma"], "ffma2_per_s": out["ffma2"], "ex2_per_s": out["ex2"],
+            "lds_bytes_per_s": out["lds128"], "sms": sms, "sm_mhz": mhz, "per_sm_per_clock": per_clk,
+            "how": "gs_peak_probe: one resident wave of 8-chain loops per unit, CUDA events, best of 3"}
 
 
 def load_peaks():
@@ -378,8 +456,11 @@ def run_ours(args, rank, world, device):
     ev_f, ev_b = int(stats.n_evals_fwd), int(stats.n_evals_bwd)
     nbl = int(stats.n_blended)   # (pixel, splat) pairs blended: the compositing's algorithmic unit
     hbm = peaks["hbm_gbs"]
-    alu_peak = N_SM * FP32_LANES * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # T lane-ops/s
-    OPS_FWD, OPS_BWD = 20, 55
+    units = measure_unit_peaks(device)
+    # an FMA counts as one operation; the kernels use packed FP32x2 operations
+    # where they can, so the FP32 roof is the faster of the two measured rates
+    alu_peak = max(units["ffma_per_s"], units["ffma2_per_s"]) / 1e12   # T ops/s
+    mufu_peak = units["ex2_per_s"] / 1e12
     gbytes = 4 * (3 + 3 + 4 + 1)          # geometry + opacity of one Gaussian
     shbytes = pbytes - gbytes             # its SH coefficients
     algo = {
@@ -390,8 +471,8 @@ def run_ours(args, rank, world, device):
         "bin": ("hbm", P * 24 + nvis * 16 + N * 8),
         # ops: per blended (pixel, splat) pair (Eq. 3 sums over these); the
         # evaluations the kernels spend on splats that end up not blended are overhead
-        "render_fwd": ("alu", nbl * OPS_FWD),
-        "composite_bwd": ("alu", nbl * OPS_BWD),
+        "render_fwd": ("alu", (nbl * OPS_FWD, nbl * MUFU_FWD)),
+        "composite_bwd": ("alu", (nbl * OPS_BWD, nbl * MUFU_BWD)),
         # bytes: key of every entry, parameters + 2D gradients of visible entries read,
         # all parameter gradients written
         "preprocess_bwd": ("hbm", N * 4 + nvis * (pbytes + 64) + N * pbytes),
@@ -404,22 +485,49 @@ def run_ours(args, rank, world, device):
             roof[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                        "frac": round(ach / hbm, 4), "bytes": int(work), "ms": round(stages[k], 4)}
         else:
-            ach = work / t_s / 1e12
-            roof[k] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
-                       "unit": "Tops/s", "frac": round(ach / alu_peak, 4), "ops": int(work),
-                       "ms": round(stages[k], 4)}
+            ops, mufu = work
+            a_alu, a_mufu = ops / t_s / 1e12, mufu / t_s / 1e12
+            f_alu, f_mufu = a_alu / alu_peak, a_mufu / mufu_peak
+            if f_alu >= f_mufu:
+                roof[k] = {"bound": "alu", "achieved": round(a_alu, 3), "peak": round(alu_peak, 2),
+                           "unit": "Tops/s", "frac": round(f_alu, 4)}
+            else:
+                roof[k] = {"bound": "mufu", "achieved": round(a_mufu, 3), "peak": round(mufu_peak, 3),
+                           "unit": "Tops/s", "frac": round(f_mufu, 4)}
+            roof[k].update({"ops": int(ops), "mufu_ops": int(mufu), "ms": round(stages[k], 4),
+                            "fp32": {"achieved": round(a_alu, 3), "peak": round(alu_peak, 2), "frac": round(f_alu, 4)},
+                            "mufu": {"achieved": round(a_mufu, 4), "peak": round(mufu_peak, 3),
+                                     "frac": round(f_mufu, 4)}})
     traffic = load_traffic(args.config)
     for k in roof:
         roof[k]["traffic"] = traffic.get(k)
+    # the unit the compositing kernels saturate, from the committed ncu counters of
+    # the current sources: shared-memory wavefronts (128 B each) per launch / the
+    # live launch time, against the measured shared-memory peak
+    counters = load_counters(args.config)
+    for k, kern in (("render_fwd", "k_render_fwd"), ("composite_bwd", "k_render_bwd")):
+        c = counters.get(kern)
+        if c:
+            t_s = stages[k] * 1e-3
+            sm_bps = c["smem_wavefronts"] * 128 / t_s
+            roof[k]["binding"] = {
+                "unit": "shared-memory wavefronts (L1 data pipe)",
+                "achieved_gbs": round(sm_bps / 1e9, 1), "peak_gbs": round(units["lds_bytes_per_s"] / 1e9, 1),
+                "frac": round(sm_bps / units["lds_bytes_per_s"], 4),
+                "issue_active": c.get("issue_active"), "source": "ncu wavefronts per launch / event time"}
     # the whole frame: every stage at its own peak, against the measured step
-    t_roof = sum((work / (hbm * 1e9) if bound == "hbm" else work / (alu_peak * 1e12)) * 1e3
-                 for bound, work in algo.values())
+    def t_at_peak(bound, work):
+        if bound == "hbm":
+            return work / (hbm * 1e9)
+        return max(work[0] / (alu_peak * 1e12), work[1] / (mufu_peak * 1e12))
+    t_roof = sum(t_at_peak(bound, work) * 1e3 for bound, work in algo.values())
     frame_roof = {"ms_at_peaks": round(t_roof, 4), "frac": round(t_roof / ms, 4),
                   "how": "sum over the stages of algorithmic work / that stage's peak, divided by value"}
     dom = max(stages, key=lambda k: stages[k])
     r = dict(roof[dom])
     r["kernel"] = dom
-    r["peak_source"] = f"{src} ({'MEASURED_PEAKS.json' if src == 'measured' else 'recipe fallback'})"
+    r["peak_source"] = (f"HBM: {src} ({'MEASURED_PEAKS.json' if src == 'measured' else 'recipe fallback'}); "
+                        "FP32, MUFU and shared memory: measured in this run (unit_peaks)")
     out = {
         "metric": METRIC, "value": round(ms, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": False,
@@ -431,7 +539,7 @@ def run_ours(args, rank, world, device):
         "ms_per_step_eager": round(ms_eager, 4),
         "roofline": r, "stages": roof, "frame_roofline": frame_roof,
         "counts": {"visible": nvis, "pairs": P, "blended": nbl, "evals_fwd": ev_f, "evals_bwd": ev_b},
-        "clocks": clocks, "e2e": e2e,
+        "clocks": clocks, "e2e": e2e, "unit_peaks": units,
         "gpu_launches": launches_per_step(frame_tiles(cam, params)) * args.steps,
     }
     return out
@@ -477,6 +585,45 @@ def run_bf16(args, device):
     return {"workload": "unbounded scene, 3M Gaussians, BF16 storage, FP32 compositing, 1297x840",
             "ms_per_step_graph": round(ms, 4), "ms_per_step_eager": round(eager, 4),
             "param_bytes": int(sum(getattr(st, k).numel() * 2 for k in ("means", "scales", "quats", "opacities", "sh")))}
+
+
+def run_batched_bf16(args, device, plain_ms, n_views=4):
+    """The precision pattern's headline comparison: several 1297x840 views of the
+    3M scene rendered and differentiated together (one launch per kernel, one
+    CUDA graph, tile autotuned) with every parameter stored in BF16 and FP32
+    compositing, against the plain FP32 single-view step; the same batch with
+    FP32 storage separates the two effects."""
+    import torch
+    from paper_2406_01467_b300 import Frame, RenderParams, SceneTensors, autotune, scenes
+    scene, _ = make_workload("unbounded")
+    views = [(c, 0) for c in scenes.fusion_cameras(n_views, seed=7)]
+    out = {"workload": f"unbounded scene, 3M Gaussians, {n_views} views 1297x840 in one frame, fwd+bwd, "
+                       "one CUDA graph, autotuned tile", "views": n_views,
+           "plain_fp32_single_view_ms": round(plain_ms, 4)}
+    for name, dt in (("bf16", torch.bfloat16), ("fp32", torch.float32)):
+        st = SceneTensors.from_scene(scene, device, dt)
+        params, rep = autotune.tune_tile([st], views, RenderParams(), iters=3, cache_path=None,
+                                         candidates=((16, 16), (16, 8), (32, 8)))
+        fr = Frame([st], views, params)
+        fr.forward()
+        need = int(fr.stats().n_pairs)
+        fr._alloc(int(need * 1.25) + 1024)
+        g = torch.Generator(device=device).manual_seed(13)
+        up = [torch.randn(k * fr.n_pixels, device=device, generator=g) for k in (3, 1, 1, 3)]
+        step = autotune.make_step(fr, up, fr.alloc_grads())
+        ms, eager = timed_graph(step, max(10, args.steps // 4), args.warmup)
+        fr.stats()
+        if fr.last_status != 0:
+            raise RuntimeError(f"batched {name} frame status {fr.last_status}")
+        out[name] = {"ms_per_batch_graph": round(ms, 4), "ms_per_view": round(ms / n_views, 4),
+                     "ms_per_batch_eager": round(eager, 4), "tile": f"{params.tile_w}x{params.tile_h}",
+                     "autotune_ms": rep["all"], "pairs": need,
+                     "param_bytes": int(sum(getattr(st, k).numel() * getattr(st, k).element_size()
+                                            for k in ("means", "scales", "quats", "opacities", "sh")))}
+        del fr, step, st
+        torch.cuda.empty_cache()
+    out["bf16_ms_per_view_over_fp32_single_view"] = round(out["bf16"]["ms_per_view"] / plain_ms, 4)
+    return out
 
 
 def run_regularized(args, device, plain_ms):
@@ -609,12 +756,14 @@ def run_batched(args, device):
 # --------------------------------------------------------------------------------------
 # CPU oracle (baseline arm and cpu_baseline field)
 # --------------------------------------------------------------------------------------
-def oracle_sample(scene, cam, crop=32, n_crops=1, seed=0):
-    """Time the FP64 oracle on a bounded sample: its FP32 binning decisions over
-    all Gaussians, then forward + gradients for ``n_crops`` crops of crop x crop
-    pixels restricted to the Gaussians whose rectangles reach them.  Returns the
-    estimated ms for a whole frame and the measured seconds."""
-    import torch
+def oracle_step(scene, cam, seed, crop=32, grid=4):
+    """One step of the CPU oracle on a bounded sample of the frame: its FP32
+    binning decisions over all Gaussians, then forward + gradients for grid x
+    grid crops of crop x crop pixels, one at a seeded position in each cell of
+    a grid x grid partition of the image (stratified, so every step samples
+    the whole frame), each restricted to the Gaussians whose rectangles reach
+    it.  Returns (estimated ms for the whole frame, seconds spent, sampled
+    pixels): binning time + crop time scaled by pixels."""
     import oracle
     from oracle import binning
     from paper_2406_01467_b300 import scenes
@@ -627,45 +776,65 @@ def oracle_sample(scene, cam, crop=32, n_crops=1, seed=0):
     dec = binning.decide(scene.means, scene.scales, scene.quats, scene.opacities, cam, p)
     t_dec = time.perf_counter() - t0
     rng = np.random.default_rng(seed)
-    t_crop = 0.0
     up = [u[0] for u in scenes.upstream_grads(11, cam.height, cam.width)]
-    for _ in range(n_crops):
-        x0 = int(rng.integers(0, cam.width - crop))
-        y0 = int(rng.integers(0, cam.height - crop))
-        r = dec["rect"]
-        sel = dec["valid"] & (r[:, 1] >= x0) & (r[:, 0] < x0 + crop) & (r[:, 3] >= y0) & (r[:, 2] < y0 + crop)
-        sub = scene.subset(np.nonzero(sel)[0])
-        ys, xs = np.mgrid[y0:y0 + crop, x0:x0 + crop]
-        pix = (ys * cam.width + xs).reshape(-1)
-        t1 = time.perf_counter()
-        oracle.render_grads(sub, cam, up, p, pixels=pix)
-        t_crop += time.perf_counter() - t1
-    npix = cam.width * cam.height
-    est_ms = (t_dec + t_crop / (n_crops * crop * crop) * npix) * 1e3
-    return est_ms, t_dec + t_crop, torch.get_num_threads(), \
-        f"FP32 binning of all {scene.n} Gaussians + fwd/grad of {n_crops} crop(s) of {crop}x{crop} px, " \
-        f"scaled by {npix}/{n_crops * crop * crop} pixels"
+    r = dec["rect"]
+    t_crop, n_pix = 0.0, 0
+    cw, ch = cam.width // grid, cam.height // grid
+    for gy in range(grid):
+        for gx in range(grid):
+            x0 = gx * cw + int(rng.integers(0, max(1, cw - crop)))
+            y0 = gy * ch + int(rng.integers(0, max(1, ch - crop)))
+            sel = dec["valid"] & (r[:, 1] >= x0) & (r[:, 0] < x0 + crop) & (r[:, 3] >= y0) & (r[:, 2] < y0 + crop)
+            sub = scene.subset(np.nonzero(sel)[0])
+            ys, xs = np.mgrid[y0:y0 + crop, x0:x0 + crop]
+            pix = (ys * cam.width + xs).reshape(-1)
+            t1 = time.perf_counter()
+            oracle.render_grads(sub, cam, up, p, pixels=pix)
+            t_crop += time.perf_counter() - t1
+            n_pix += len(pix)
+    est_ms = (t_dec + t_crop / n_pix * (cam.width * cam.height)) * 1e3
+    return est_ms, t_dec + t_crop, n_pix
+
+
+def oracle_baseline(scene, cam, seeds, single_thread=True):
+    """The oracle timed on this host over the steps ``seeds`` (oracle_step), and
+    once more on one thread.  Both arms of the benchmark use this sample."""
+    import torch
+    cores = torch.get_num_threads()
+    est, secs, pix = zip(*[oracle_step(scene, cam, sd) for sd in seeds])
+    out = {"value": round(float(np.mean(est)), 1), "unit": "ms", "cores": cores, "kind": "oracle",
+           "steps": len(seeds), "extrapolated": True, "sampled_pixels_per_step": int(pix[0]),
+           "frame_pixels": int(cam.width * cam.height), "seconds": round(float(sum(secs)), 1),
+           "sample": f"per step: FP32 binning of all {scene.n} Gaussians + forward and gradients of 16 "
+                     f"crops of 32x32 px (one per cell of a 4x4 grid, seeded by the step), the crop time "
+                     f"scaled by {cam.width * cam.height}/{pix[0]} pixels",
+           "spread_ms": [round(float(min(est)), 1), round(float(max(est)), 1)]}
+    if single_thread:
+        torch.set_num_threads(1)
+        try:
+            e1, s1, _ = oracle_step(scene, cam, seeds[0])
+        finally:
+            torch.set_num_threads(cores)
+        out["single_thread_value"] = round(float(e1), 1)
+    return out
 
 
 def run_reference(args, world):
     scene, cam = make_workload(args.config)
-    for _ in range(args.warmup):
-        oracle_sample(scene, cam, seed=1000 + _)
-    vals, secs = [], 0.0
-    for k in range(args.steps):
-        est, s, cores, sample = oracle_sample(scene, cam, seed=k)
-        vals.append(est)
-        secs += s
-    v = float(np.mean(vals))
+    for k in range(args.warmup):
+        oracle_step(scene, cam, 1000 + k)
+    base = oracle_baseline(scene, cam, list(range(args.steps)), single_thread=False)
+    v = base["value"]
     out = {
-        "metric": METRIC, "value": round(v, 2), "unit": "ms", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(v, 2), "higher_is_better": False, "scaling": "weak",
+        "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "extrapolated": True,
+        "sample_seconds_per_step": round(base["seconds"] / args.steps, 2),
         "config": {"workload": CONFIGS[args.config]["workload"], "gaussians": scene.n,
                    "image": f"{cam.width}x{cam.height}", "parallelism": "cpu"},
-        "cpu_baseline": {"value": round(v, 2), "unit": "ms", "cores": cores, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": round(v, 2), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": base,
+        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     return out
 
@@ -701,15 +870,15 @@ def main():
     out = run_ours(args, rank, world, f"cuda:{local}")
     if not args.no_extras and args.config == "unbounded":
         out["bf16_graph"] = run_bf16(args, f"cuda:{local}")
+        out["batched_bf16"] = run_batched_bf16(args, f"cuda:{local}", out["ms_per_step"])
         out["regularized"] = run_regularized(args, f"cuda:{local}", out["ms_per_step"])
         out["filtered"] = run_filtered(args, f"cuda:{local}")
         out["batched"] = run_batched(args, f"cuda:{local}")
         out["geometry_views"] = run_geometry(args, f"cuda:{local}")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the reference arm's first four steps, plus one on a single thread
         scene, cam = make_workload(args.config)
-        est, secs, cores, sample = oracle_sample(scene, cam, n_crops=64)
-        out["cpu_baseline"] = {"value": round(est, 1), "unit": "ms", "cores": cores, "kind": "oracle",
-                               "sample": sample, "seconds": round(secs, 1)}
+        out["cpu_baseline"] = oracle_baseline(scene, cam, [0, 1, 2, 3])
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

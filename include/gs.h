@@ -336,6 +336,24 @@ gs_status gs_check(const gs_frame* frame, gs_stats* out, void* stream);
  * frame must have been prepared as for gs_preprocess. */
 gs_status gs_debug_wait_timeout(const gs_frame* frame, int32_t spin_limit, void* stream);
 
+/* ---- Throughput probes (measurement support; the paper has no counterpart) --
+ * The compositing kernels are bound by instruction issue, the FP32 and MUFU
+ * pipes and shared memory rather than by HBM; these probes measure those
+ * units' peak rates on the GPU at hand so that a benchmark can state the
+ * kernels' fractions of them.  Each call enqueues on `stream` (a cudaStream_t)
+ * one resident wave of blocks (every SM, as many blocks as fit) that runs
+ * long chains of one operation, and stores in *work (host) how many of them
+ * the launch performs: FMAs (GS_PEAK_FFMA: scalar fma.rn.f32; GS_PEAK_FFMA2:
+ * packed fma.rn.f32x2, two FMAs per instruction), base-2 exponentials
+ * (GS_PEAK_EX2: ex2.approx.ftz.f32) or bytes read from shared memory
+ * (GS_PEAK_LDS128: 16-byte loads, consecutive per lane, no bank conflicts).
+ * The caller times the launch.  `iters` (1 .. 2^24) sets its length: each
+ * thread runs 16 * iters steps of 8 independent chains.  `sink` is a device
+ * float the probe never actually writes.  GS_ERR_INVALID_ARG for a bad kind,
+ * count or pointer; GS_ERR_CUDA if the launch fails. */
+enum { GS_PEAK_FFMA = 0, GS_PEAK_FFMA2 = 1, GS_PEAK_EX2 = 2, GS_PEAK_LDS128 = 3 };
+gs_status gs_peak_probe(int32_t kind, int32_t iters, float* sink, int64_t* work, void* stream);
+
 /* Human-readable description of the calling thread's last error. */
 const char* gs_last_error_string(void);
 

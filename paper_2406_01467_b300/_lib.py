@@ -78,7 +78,8 @@ class GsStats(Structure):
 EXPORTS = ("gs_workspace_size", "gs_preprocess", "gs_bin", "gs_render_fwd", "gs_render_bwd",
            "gs_composite_bwd", "gs_preprocess_bwd", "gs_filter3d", "gs_appearance_param_count",
            "gs_appearance_fwd_bwd", "gs_adam_step", "gs_debug_copy", "gs_render_fwd_static",
-           "gs_check", "gs_debug_wait_timeout", "gs_last_error_string")
+           "gs_check", "gs_debug_wait_timeout", "gs_peak_probe", "gs_last_error_string")
+GS_PEAK_FFMA, GS_PEAK_FFMA2, GS_PEAK_EX2, GS_PEAK_LDS128 = range(4)
 STATIC_SCRATCH_BYTES = 32 << 20
 
 _lib = None
@@ -132,6 +133,8 @@ def load(path: str = LIB_PATH):
     lib.gs_check.restype = c_int32
     lib.gs_debug_wait_timeout.argtypes = [pf, c_int32, c_void_p]
     lib.gs_debug_wait_timeout.restype = c_int32
+    lib.gs_peak_probe.argtypes = [c_int32, c_int32, c_void_p, POINTER(c_int64), c_void_p]
+    lib.gs_peak_probe.restype = c_int32
     lib.gs_last_error_string.argtypes = []
     lib.gs_last_error_string.restype = ctypes.c_char_p
     _lib = lib

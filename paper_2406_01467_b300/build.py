@@ -7,7 +7,8 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SOURCES = ["abi.cu", "preprocess.cu", "binning.cu", "composite.cu", "losses.cu", "appearance.cu", "static_scratch.cu"]
+SOURCES = ["abi.cu", "preprocess.cu", "binning.cu", "composite.cu", "losses.cu", "appearance.cu", "static_scratch.cu",
+           "peaks.cu"]
 LIB = os.path.join(HERE, "libgs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
