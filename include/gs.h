@@ -313,7 +313,11 @@ gs_status gs_debug_copy(const gs_frame* frame, float* rec, int32_t* rect,
  *
  * The first call on a device, with that device current, looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  No call runs cudaMalloc, cudaFree or an allocating library
+ * stream capture.  The address is kept per device together with the id of
+ * the device's CUDA context, and looked up again when a call finds another
+ * context current (after cudaDeviceReset, or a primary context released and
+ * re-created); the first call after such a reset should also precede any
+ * capture.  No call runs cudaMalloc, cudaFree or an allocating library
  * routine.  All calls share the one array and each call re-initialises what
  * must start at zero (counters, status word, tile ranges), so consecutive calls
  * are independent; calls whose work overlaps on the GPU (other streams or

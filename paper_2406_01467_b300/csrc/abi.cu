@@ -211,7 +211,7 @@ static gs_status prepare_ws(const gs_frame* f, FrameDev& fd, Layout& L) {
 // the parameter words are read from the constant bank, where the lanes' distinct
 // addresses serialise, so the unused view and scene slots (most of the 11 KB)
 // are left out; no kernel reads them.
-__global__ void k_setup(FrameDev fd, FrameDev* dst, Header* hdr) {
+__global__ void k_setup(FrameDev fd, FrameDev* dst, Header* hdr, BwdCounters* bc) {
   const uint32_t* src = reinterpret_cast<const uint32_t*>(&fd);
   uint32_t* d = reinterpret_cast<uint32_t*>(dst);
   const int nv = fd.n_views, ns = fd.n_scenes;
@@ -228,6 +228,9 @@ __global__ void k_setup(FrameDev fd, FrameDev* dst, Header* hdr) {
   copy(offsetof(FrameDev, n_views), sizeof(FrameDev) - offsetof(FrameDev, n_views));
   uint32_t* h = reinterpret_cast<uint32_t*>(hdr);
   for (int i = threadIdx.x; i < (int)(sizeof(Header) / 4); i += blockDim.x) h[i] = 0u;
+  // the backward's counters too, so a frame rendered without a backward reports
+  // no backward evaluations (the backward re-clears them before it runs)
+  if (bc && threadIdx.x == 0) *bc = BwdCounters{0, 0, 0};
 }
 
 static_assert(sizeof(FrameDev) % 4 == 0, "FrameDev must be a whole number of words");
@@ -238,7 +241,8 @@ static_assert(sizeof(ViewDev) % 4 == 0 && sizeof(SceneDev) % 4 == 0 && offsetof(
 static_assert(sizeof(Header) == 256, "Header is one 256-byte block");
 
 cudaError_t launch_setup(const FrameDev& fd, void* ws, const Layout& L, cudaStream_t s) {
-  k_setup<<<1, 256, 0, s>>>(fd, at<FrameDev>(ws, L.frame), at<Header>(ws, L.hdr));
+  k_setup<<<1, 256, 0, s>>>(fd, at<FrameDev>(ws, L.frame), at<Header>(ws, L.hdr),
+                            fd.geometry_only ? nullptr : at<BwdCounters>(ws, L.bwdcnt));
   return cudaGetLastError();
 }
 
@@ -257,6 +261,15 @@ __global__ void k_debug_grad2d(const float4* src, const uint32_t* key, int64_t E
     out[i] = key[i >> 2] == kInvalidKey ? make_float4(0.f, 0.f, 0.f, 0.f) : src[i];
 }
 
+gs_status frame_workspace_size(const gs_frame* frame, size_t* bytes) {
+  FrameDev fd;
+  Layout L;
+  *bytes = 0;
+  const gs_status st = prepare(frame, fd, L);
+  if (st == GS_OK) *bytes = L.total;
+  return st;
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -264,10 +277,8 @@ using namespace gs;
 extern "C" {
 
 size_t gs_workspace_size(const gs_frame* frame) {
-  FrameDev fd;
-  Layout L;
-  if (prepare(frame, fd, L) != GS_OK) return 0;
-  return L.total;
+  size_t bytes = 0;
+  return frame_workspace_size(frame, &bytes) == GS_OK ? bytes : 0;
 }
 
 gs_status gs_preprocess(const gs_frame* frame, void* stream) {

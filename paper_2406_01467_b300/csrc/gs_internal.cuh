@@ -199,6 +199,8 @@ int tile_sort_bits(int64_t n_tiles);
 
 // Sets the calling thread's error string (printf-style) and returns `s`.
 gs_status set_error(gs_status s, const char* fmt, ...);
+// gs_workspace_size with the validation status (the error string says why).
+gs_status frame_workspace_size(const gs_frame* frame, size_t* bytes);
 
 // ---- launchers (each .cu file owns its kernels) ---------------------------
 cudaError_t launch_setup(const FrameDev& fd, void* ws, const Layout& L, cudaStream_t s);

@@ -209,3 +209,15 @@ def test_backward_run_to_run_differences_are_bounded():
     fr2 = _frame(sc, cam, p)
     for a, b in zip(fr.view_maps(0), fr2.view_maps(0)):
         torch.testing.assert_close(a, b, rtol=0, atol=0)
+
+
+def test_forward_after_backward_reports_no_backward_evaluations():
+    # every gs_preprocess clears the backward's counters as well as the header's,
+    # so gs_check after a forward-only frame does not report an older backward
+    sc, cam = scenes.tiny_scene(), scenes.tiny_camera()
+    fr = _frame(sc, cam, RenderParams())
+    fr.backward(*[torch.from_numpy(u[0]).to(DEV) for u in scenes.upstream_grads(3, cam.height, cam.width)])
+    assert fr.stats().n_evals_bwd > 0
+    fr.forward()
+    st = fr.stats()
+    assert st.n_evals_bwd == 0 and st.n_evals_fwd > 0 and st.status == 0

@@ -77,6 +77,7 @@ def test_static_scratch_forward_matches_caller_workspace_twice():
                                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
         assert status == _lib.GS_OK, lib.gs_last_error_string().decode()
         assert stats.n_pairs == ref.stats().n_pairs and stats.n_visible == ref.stats().n_visible
+        assert stats.n_evals_bwd == 0 and stats.status == _lib.GS_OK   # no backward ran in this call
         for got, want in zip(outs, (ref.color, ref.alpha, ref.depth, ref.normal)):
             # same kernels on the same inputs: within the parity tolerance (in fact equal)
             torch.testing.assert_close(got, want, rtol=0, atol=1e-6)
