@@ -32,10 +32,13 @@
 // recovering T by division (alpha <= alpha_max < 1) and the colour / normal
 // "behind" sums recursively; nothing per (pixel, splat) is stored.  It replays
 // only the records the forward marked as blended by some pixel of the warp's
-// block, two per round.  Each warp reduces the 15 per-splat sums of its 32
+// block, two per round.  Each warp reduces the per-splat sums of its 32
 // pixels (one shuffle fold, then a transpose through shared memory) and issues
 // one atomic per sum; the sums are linear in the splat's conic, p and opacity,
-// which the preprocess backward applies once per entry.
+// which the preprocess backward applies once per entry.  Without Eq. 23 only a
+// pixel's median splat gets a depth gradient, so the three depth sums leave the
+// reduction (12 values instead of 16) and the lanes whose median is the
+// record add them with atomics of their own.
 // Eq. 23 with constant weights adds dL/dd_k = 4 w_k W (d_k - mean) to each
 // contributor's planar depth; Eq. 24 enters through the map gradients of
 // alpha, normal and depth that the normal-consistency backward stored.
@@ -316,23 +319,31 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
 }
 
 // Warp reduction of the gradient slots of one or two records.  First lanes l
-// and l^16 fold their 16 values with shuffles: in each of four pairs of
-// float2 slots the lower lane keeps one (P_k) and the upper lane the other
-// (Q_k), each summed over both lanes; every lane computes the half it keeps
-// and the half it sends, choosing them by its half of the warp as cheaply as
-// the slot's form allows.  The 8 kept values then go to the warp's shared
-// scratch as rows red[row][lane] (rows 0-7: record A, 8-15: record B; stride
-// kRedStride = 36 floats keeps the row stores and the 16-byte loads free of
-// bank conflicts), and lane l adds the half row holding value l & 15 of record
-// l >> 4 with four 16-byte loads: P_k (k = (l & 7) >> 1) for l & 15 < 8, else
-// Q_k.  The shuffle fold halves the shared-memory traffic of a transpose
-// through shared memory.
+// and l^16 fold their values with shuffles: in each of NP pairs of float2
+// slots the lower lane keeps one (P_k) and the upper lane the other (Q_k),
+// each summed over both lanes; every lane computes the half it keeps and the
+// half it sends, choosing them by its half of the warp as cheaply as the
+// slot's form allows.  The 2 NP kept values then go to the warp's shared
+// scratch as rows red[row][lane] (rows 0 .. 2NP-1: record A, 2NP .. 4NP-1:
+// record B; stride kRedStride = 36 floats keeps the row stores and the 16-byte
+// loads free of bank conflicts), and lane l adds the half row holding value
+// s = l & 15 of record l >> 4 with four 16-byte loads: P_k for s < 2 NP, Q_k
+// for 2 NP <= s < 4 NP.  The shuffle fold halves the shared-memory traffic of
+// a transpose through shared memory.
+//
+// NP = 4 (16 values) carries the splat's planar-depth sums S sd, S sd dx,
+// S sd dy; it serves Eq. 23, whose gradient reaches the depth of every
+// contributor.  Without it only the median splat of a pixel receives a depth
+// gradient (one splat per pixel), so NP = 3 (12 values) leaves those three
+// sums out of the reduction and the few lanes whose median is the record add
+// them with atomics of their own.
 constexpr int kRedStride = 36;
 
-__device__ inline void fold_store(const float2 (&keep)[4], const float2 (&send)[4], float* __restrict__ rows) {
+template <int NP>
+__device__ inline void fold_store(const float2 (&keep)[NP], const float2 (&send)[NP], float* __restrict__ rows) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < NP; ++k) {
     const float2 recv = make_float2(__shfl_xor_sync(kFull, send[k].x, 16), __shfl_xor_sync(kFull, send[k].y, 16));
     const float2 h = __fadd2_rn(keep[k], recv);
     rows[(2 * k) * kRedStride + lane] = h.x;
@@ -340,26 +351,31 @@ __device__ inline void fold_store(const float2 (&keep)[4], const float2 (&send)[
   }
 }
 
-// The record slot that reduced value s = lane & 15 adds to (4 bits per value):
-// P0 = gs d -> (U, V); P1 = w (dC0, dC1) -> (R, G); P2 = (gs dy^2, gs) -> (CC, O);
-// P3 = sd d -> (P0, P1); Q0 = gs dx d -> (CA, CB); Q1 = w (dC2, dN0) -> (B, N0);
-// Q2 = (0, sd) -> (CUT, Z); Q3 = w (dN1, dN2) -> (N1, N2).
-constexpr unsigned long long kFoldSlots = 0xba76fe329854dc10ull;
+// The record slot that reduced value s = lane & 15 adds to (4 bits per value).
+// NP = 4: P0 = gs d -> (U, V); P1 = w (dC0, dC1) -> (R, G); P2 = (gs dy^2, gs)
+// -> (CC, O); P3 = sd d -> (P0, P1); Q0 = gs dx d -> (CA, CB); Q1 = w (dC2, dN0)
+// -> (B, N0); Q2 = (0, sd) -> (CUT, Z); Q3 = w (dN1, dN2) -> (N1, N2).
+// NP = 3: P0, P1, P2, Q0, Q1 as above; Q2 = w (dN1, dN2) -> (N1, N2); values
+// 12-15 are unused.
+constexpr unsigned long long kFoldSlots4 = 0xba76fe329854dc10ull;
+constexpr unsigned long long kFoldSlots3 = 0x6666bafe3254dc10ull;
 
+template <int NP>
 __device__ inline float reduce_rows(const float* __restrict__ red) {
   const int lane = threadIdx.x & 31, s = lane & 15;
-  const float4* q =
-      reinterpret_cast<const float4*>(red + ((lane >> 4) * 8 + (s & 7)) * kRedStride + (s >> 3) * 16);
+  if (s >= 4 * NP) return 0.f;
+  const int q = s >= 2 * NP;   // the Q half of the row
+  const float4* r =
+      reinterpret_cast<const float4*>(red + ((lane >> 4) * 2 * NP + s - q * 2 * NP) * kRedStride + q * 16);
   float2 h[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const float4 a = q[i];
+    const float4 a = r[i];
     h[i] = __fadd2_rn(make_float2(a.x, a.y), make_float2(a.z, a.w));
   }
   const float2 t = __fadd2_rn(__fadd2_rn(h[0], h[1]), __fadd2_rn(h[2], h[3]));
   return t.x + t.y;
 }
-
 // One backward work item (same decomposition as fwd_item): the warp replays
 // its pixels from their last contributors toward the front of the list.
 template <bool LOSS>
@@ -412,16 +428,29 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
     }
   }
   const int wmax = __reduce_max_sync(kFull, last);
+  constexpr int NP = LOSS ? 4 : 3;   // float2 pairs per lane in the fold
+  if (!LOSS && med >= 0 && dD != 0.f) {
+    // Without Eq. 23 the depth map's gradient reaches the pixel's median splat
+    // only (a contributor by definition): d = z_c + p . Delta there, so its
+    // depth sums gain dD (1, dx, dy), added here once per pixel instead of in
+    // every visit's reduction
+    const uint32_t e = pval[med];
+    const float4 a = rec[4 * (int64_t)e];
+    float* row = grad + (int64_t)e * kRecFloats;
+    atomicAdd(row + G_Z, dD);
+    atomicAdd(row + G_P0, dD * (a.x - fpx));
+    atomicAdd(row + G_P1, dD * (a.y - fpy));
+  }
 
   float T = Tf;
   const float dATf = dA * Tf;
   // running "behind" sums of (r, g, b, n0, n1, n2) and the upstream of the same six, as pairs
   float2 S01 = make_float2(0.f, 0.f), S23 = make_float2(0.f, 0.f), S45 = make_float2(0.f, 0.f);
   const float2 U01 = make_float2(dC[0], dC[1]), U23 = make_float2(dC[2], dN[0]), U45 = make_float2(dN[1], dN[2]);
-  // the fold's pairs: lanes 0-15 keep P_k, lanes 16-31 Q_k (kFoldSlots)
+  // the fold's pairs: lanes 0-15 keep P_k, lanes 16-31 Q_k (kFoldSlots4 / kFoldSlots3)
   const bool hi = lane & 16;
   const float2 Ukeep = hi ? U23 : U01, Usend = hi ? U01 : U23;
-  const int slot = (int)((kFoldSlots >> (4 * (lane & 15))) & 15u);
+  const int slot = (int)(((LOSS ? kFoldSlots4 : kFoldSlots3) >> (4 * (lane & 15))) & 15u);
   const float2 nfp = make_float2(-fpx, -fpy);
   // the forward's per-chunk masks name the records some lane of this block
   // blended; the others have zero gradient here and are not replayed
@@ -450,8 +479,9 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       // (S gs dx, S gs dy) (S gs dx^2, S gs dx dy) (S gs dy^2, S gs) (0, S sd)
       // (S sd dx, S sd dy), with gs = dL/dsigma and sd = dL/dd; the preprocess
       // backward applies the constants once per entry.  They are folded in the
-      // pairs (P_k, Q_k) of kFoldSlots: this lane keeps one half, sends the other
-      float2 keep[4], send[4];
+      // pairs (P_k, Q_k) of kFoldSlots4 / kFoldSlots3: this lane keeps one half,
+      // sends the other
+      float2 keep[NP], send[NP];
       const bool live = idx <= last;
       // the depth plane (p, z) only for Eq. 23
       const float4 a = my[0][j], b = my[1][j], e3 = my[3][j];
@@ -486,11 +516,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       S45 = __ffma2_rn(al2, q2, S45);
       const float dal = contrib ? T * (acc.x + acc.y) + dATf * ia : 0.f;
       // d = z_c + p . Delta (Eq. 4): the median splat, and Eq. 23 with the weights constant
-      float sd = (contrib && idx == med) ? dD : 0.f;
-      if (LOSS) sd += c4 * w * ((e2.z + e2.x * dx + e2.y * dy) - dmean);
-      const float2 p3 = __fmul2_rn(make_float2(sd, sd), d), q3 = __fmul2_rn(w2, U45);
-      keep[3] = hi ? q3 : p3;            // sd d | w (dN1, dN2)
-      send[3] = hi ? p3 : q3;
+      const float2 qn = __fmul2_rn(w2, U45);   // w (dN1, dN2)
       // alpha = o G below the clamp: dL/dsigma = -dL/dalpha alpha
       const float gs = raw <= amax ? -dal * al : 0.f;
       const float gsx = gs * dx;
@@ -498,9 +524,19 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       keep[0] = __fmul2_rn(make_float2(sk, sk), d);   // gs d | gs dx d
       send[0] = __fmul2_rn(make_float2(ss, ss), d);
       const float gy2 = gs * d2.y;
-      keep[2] = make_float2(hi ? 0.f : gy2, hi ? sd : gs);   // (gs dy^2, gs) | (0, sd)
-      send[2] = make_float2(hi ? gy2 : 0.f, hi ? gs : sd);
-      fold_store(keep, send, rows);
+      if constexpr (LOSS) {
+        const float sd = ((contrib && idx == med) ? dD : 0.f) + c4 * w * ((e2.z + e2.x * dx + e2.y * dy) - dmean);
+        const float2 p3 = __fmul2_rn(make_float2(sd, sd), d);
+        keep[3] = hi ? qn : p3;            // sd d | w (dN1, dN2)
+        send[3] = hi ? p3 : qn;
+        keep[2] = make_float2(hi ? 0.f : gy2, hi ? sd : gs);   // (gs dy^2, gs) | (0, sd)
+        send[2] = make_float2(hi ? gy2 : 0.f, hi ? gs : sd);
+      } else {
+        const float2 p2 = make_float2(gy2, gs);
+        keep[NP - 1] = hi ? qn : p2;       // (gs dy^2, gs) | w (dN1, dN2)
+        send[NP - 1] = hi ? p2 : qn;
+      }
+      fold_store<NP>(keep, send, rows);
     };
     // some lane blends every replayed record (the forward's mask), so every
     // visit reduces.  Records go back to front, two per round where possible:
@@ -518,10 +554,10 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       visit(jA, my_red);
       if (jB >= 0) {
         m &= ~(1u << jB);
-        visit(jB, my_red + 8 * kRedStride);
+        visit(jB, my_red + 2 * NP * kRedStride);
       }
       __syncwarp();
-      const float s = reduce_rows(my_red);   // lanes 16-31 read stale rows without jB
+      const float s = reduce_rows<NP>(my_red);   // lanes 16-31 read stale rows without jB
       __syncwarp();   // the scratch is rewritten by the next round
       const int j = lane < 16 ? jA : jB;
       if (j >= 0 && slot != G_UNUSED && s != 0.f) atomicAdd(grad + (int64_t)my_e[j] * kRecFloats + slot, s);
@@ -567,7 +603,7 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
              int n_items) {
   __shared__ float4 s_rec[kRenderThreads / 32][4][32];
   __shared__ uint32_t s_ent[kRenderThreads / 32][32];
-  __shared__ __align__(16) float s_red[kRenderThreads / 32][16 * kRedStride];
+  __shared__ __align__(16) float s_red[kRenderThreads / 32][4 * (LOSS ? 4 : 3) * kRedStride];
   Header* hdr = at<Header>(ws, L.hdr);
   BwdCounters* bc = at<BwdCounters>(ws, L.bwdcnt);
   if (hdr->status == GS_ERR_CAPACITY) return;
