@@ -534,6 +534,7 @@ def run_ours(args, rank, world, device):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": CONFIGS[args.config]["workload"], "gaussians": N,
                    "image": f"{cam.width}x{cam.height}", "tile": f"{params.tile_w}x{params.tile_h}",
+                   "gaussians_per_batch": params.batch,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                    "execution": "the step as one CUDA graph, replayed"},
         "ms_per_step_eager": round(ms_eager, 4),
@@ -598,7 +599,7 @@ def run_batched_bf16(args, device, plain_ms, n_views=4):
     scene, _ = make_workload("unbounded")
     views = [(c, 0) for c in scenes.fusion_cameras(n_views, seed=7)]
     out = {"workload": f"unbounded scene, 3M Gaussians, {n_views} views 1297x840 in one frame, fwd+bwd, "
-                       "one CUDA graph, autotuned tile", "views": n_views,
+                       "one CUDA graph, autotuned tile and batch", "views": n_views,
            "plain_fp32_single_view_ms": round(plain_ms, 4)}
     for name, dt in (("bf16", torch.bfloat16), ("fp32", torch.float32)):
         st = SceneTensors.from_scene(scene, device, dt)
@@ -617,7 +618,7 @@ def run_batched_bf16(args, device, plain_ms, n_views=4):
             raise RuntimeError(f"batched {name} frame status {fr.last_status}")
         out[name] = {"ms_per_batch_graph": round(ms, 4), "ms_per_view": round(ms / n_views, 4),
                      "ms_per_batch_eager": round(eager, 4), "tile": f"{params.tile_w}x{params.tile_h}",
-                     "autotune_ms": rep["all"], "pairs": need,
+                     "gaussians_per_batch": params.batch, "autotune_ms": rep["all"], "pairs": need,
                      "param_bytes": int(sum(getattr(st, k).numel() * getattr(st, k).element_size()
                                             for k in ("means", "scales", "quats", "opacities", "sh")))}
         del fr, step, st
@@ -748,7 +749,8 @@ def run_batched(args, device):
     return {"workload": "16 views (512..1600 x 384..1200) of a 1M unbounded scene + 4 object scenes "
                         "(50K/200K/800K/2M, 800x600), FP32, one launch per kernel",
             "views": len(views), "scenes": len(sts), "entries": int(st.n_entries), "pixels": int(fr.n_pixels),
-            "pairs": int(st.n_pairs), "tile": f"{params.tile_w}x{params.tile_h}", "autotune_ms": report["all"],
+            "pairs": int(st.n_pairs), "tile": f"{params.tile_w}x{params.tile_h}",
+            "gaussians_per_batch": params.batch, "autotune_ms": report["all"],
             "ms_per_batch_graph": round(ms, 4), "ms_per_batch_eager": round(eager, 4),
             "ms_per_view_graph": round(ms / len(views), 4)}
 

@@ -111,6 +111,10 @@ typedef struct {
                              workspace shrinks by 12 B per pixel and 64 B per entry and
                              the backward calls return GS_ERR_INVALID_ARG.  Excludes
                              losses = 1. */
+  int32_t batch;          /* Gaussians a compositing warp stages in shared memory per round
+                             (the batch of records it tests against its pixels and blends):
+                             32 or 64; 0 means 32.  A performance knob only: the maps and
+                             gradients do not depend on it. */
 } gs_params;
 
 /* Everything a call needs to know about one frame (a batch of views). */

@@ -36,7 +36,7 @@ class GsParams(Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("lowpass", c_float),
                 ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float),
                 ("median_T", c_float), ("clamp_margin", c_float), ("losses", c_int32),
-                ("geometry_only", c_int32)]
+                ("geometry_only", c_int32), ("batch", c_int32)]
 
 
 class GsFrame(Structure):

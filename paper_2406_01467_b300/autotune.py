@@ -1,11 +1,14 @@
-"""Tile-size autotuning for a frame workload, and CUDA-graph capture of a step.
+"""Autotuning of the tile size and the Gaussians-per-batch for a frame
+workload, and CUDA-graph capture of a step.
 
 The maps do not depend on the tile size (a pixel's splat list and order are
-fixed by the pixel rectangles), so the tile size is a pure performance knob:
-smaller tiles give shorter lists and more (tile, splat) pairs to sort, larger
-tiles the opposite.  ``tune_tile`` times a full forward + backward step for
-each candidate on the actual frame and caches the winner per (GPU, workload
-shape) in a JSON file.
+fixed by the pixel rectangles) nor on the batch (how many records a
+compositing warp stages in shared memory per round), so both are pure
+performance knobs: smaller tiles give shorter lists and more (tile, splat)
+pairs to sort, larger tiles the opposite; larger batches halve the walk's
+per-round overhead but double the staging buffers.  ``tune_tile`` times a full
+forward + backward step for each (tile, batch) candidate on the actual frame
+and caches the winner per (GPU, workload shape) in a JSON file.
 """
 from __future__ import annotations
 
@@ -19,6 +22,7 @@ import torch
 from .rasterize import Frame, RenderParams, SceneTensors
 
 CANDIDATES: Tuple[Tuple[int, int], ...] = ((16, 16), (16, 8), (8, 16), (32, 8), (8, 8), (32, 4), (16, 4))
+BATCHES: Tuple[int, ...] = (32, 64)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gsr_tile_tuning.json")
 
 
@@ -76,8 +80,10 @@ def time_step(step: Callable, iters: int = 5) -> float:
 
 def tune_tile(scenes: Sequence[SceneTensors], views, params: Optional[RenderParams] = None,
               candidates: Sequence[Tuple[int, int]] = CANDIDATES, iters: int = 5,
-              cache_path: Optional[str] = DEFAULT_CACHE, upstream=None) -> Tuple[RenderParams, Dict]:
-    """Fastest tile size for the workload (cached).  Returns (params, report)."""
+              cache_path: Optional[str] = DEFAULT_CACHE, upstream=None,
+              batches: Sequence[int] = BATCHES) -> Tuple[RenderParams, Dict]:
+    """Fastest (tile size, Gaussians-per-batch) for the workload (cached).
+    Returns (params, report); the report's ``all`` maps "WxH/bN" to ms."""
     params = params or RenderParams()
     key = workload_key(scenes, views)
     cache = {}
@@ -87,13 +93,13 @@ def tune_tile(scenes: Sequence[SceneTensors], views, params: Optional[RenderPara
                 cache = json.load(f)
         except (OSError, ValueError):
             cache = {}
-    if key in cache:
+    if key in cache and "batch" in cache[key]:
         tw, th = cache[key]["tile"]
-        return replace(params, tile_w=tw, tile_h=th), {"cached": True, **cache[key]}
+        return replace(params, tile_w=tw, tile_h=th, batch=cache[key]["batch"]), {"cached": True, **cache[key]}
     report = {}
     best = None
-    for tw, th in candidates:
-        p = replace(params, tile_w=tw, tile_h=th)
+    for (tw, th), nb in [(c, b) for c in candidates for b in batches]:
+        p = replace(params, tile_w=tw, tile_h=th, batch=nb)
         fr = Frame(scenes, views, p)
         fr.forward()   # sizes the pair buffer
         need = int(fr.stats().n_pairs)
@@ -106,12 +112,12 @@ def tune_tile(scenes: Sequence[SceneTensors], views, params: Optional[RenderPara
             up = upstream
         step = make_step(fr, up, fr.alloc_grads())
         ms = time_step(step, iters)
-        report[f"{tw}x{th}"] = round(ms, 4)
+        report[f"{tw}x{th}/b{nb}"] = round(ms, 4)
         if best is None or ms < best[0]:
-            best = (ms, tw, th)
+            best = (ms, tw, th, nb)
         del fr
         torch.cuda.empty_cache()
-    entry = {"tile": [best[1], best[2]], "ms": round(best[0], 4), "all": report}
+    entry = {"tile": [best[1], best[2]], "batch": best[3], "ms": round(best[0], 4), "all": report}
     if cache_path:
         cache[key] = entry
         try:
@@ -120,4 +126,4 @@ def tune_tile(scenes: Sequence[SceneTensors], views, params: Optional[RenderPara
                 json.dump(cache, f, indent=1)
         except OSError:
             pass
-    return replace(params, tile_w=best[1], tile_h=best[2]), {"cached": False, **entry}
+    return replace(params, tile_w=best[1], tile_h=best[2], batch=best[3]), {"cached": False, **entry}

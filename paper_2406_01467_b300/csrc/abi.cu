@@ -71,6 +71,8 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
     return fail(GS_ERR_INVALID_ARG, "geometry_only must be 0 or 1");
   if (p.geometry_only && p.losses)
     return fail(GS_ERR_INVALID_ARG, "geometry_only excludes losses (no backward state)");
+  if (p.batch != 0 && p.batch != 32 && p.batch != 64)
+    return fail(GS_ERR_INVALID_ARG, "batch must be 0 (32), 32 or 64");
   if (f->pair_capacity < 1 || f->pair_capacity > (int64_t(1) << 31) - 1)
     return fail(GS_ERR_INVALID_ARG, "pair_capacity must be in [1, 2^31 - 1]");
 
@@ -151,6 +153,7 @@ static gs_status prepare(const gs_frame* f, FrameDev& fd, Layout& L) {
   fd.ext_c = (float)(2.0 * std::log(1.0 / (double)p.alpha_min));
   fd.losses = p.losses;
   fd.geometry_only = p.geometry_only;
+  fd.batch = p.batch == 0 ? 32 : p.batch;
 
   // ---- workspace layout ----
   memset(&L, 0, sizeof(L));

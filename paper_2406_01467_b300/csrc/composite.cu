@@ -169,29 +169,35 @@ __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\
 template <int N> __device__ inline void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
-// A chunk buffer is slot-major ([4][32] float4): lane l's 16-byte pieces sit
-// 512 bytes apart, so per-lane accesses are free of bank conflicts.  The depth
-// plane (piece 2) is staged only when every contributor's depth is needed.
+// A chunk buffer is slot-major ([slots][32] float4): lane l's 16-byte pieces
+// sit 512 bytes apart, so per-lane accesses are free of bank conflicts.  The
+// depth plane (piece 2) is staged only when every contributor's depth is
+// needed (PLANE); then the slots are pieces 0-3, else pieces 0, 1 and 3.
+template <bool PLANE> constexpr int kSlots = PLANE ? 4 : 3;
+template <bool PLANE> constexpr int kColourSlot = PLANE ? 3 : 2;   // piece 3: (r, g, b, n0)
+
 template <bool PLANE, bool L1 = true>
 __device__ inline void stage_record(float4 (*chunk)[32], int lane, const float4* r) {
   const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(&chunk[0][lane]));
   cp_async16<L1>(dst, r);
   cp_async16<L1>(dst + 512, r + 1);
   if (PLANE) cp_async16<L1>(dst + 1024, r + 2);
-  cp_async16<L1>(dst + 1536, r + 3);
+  cp_async16<L1>(dst + 512 * kColourSlot<PLANE>, r + 3);
 }
 
 // One work item: warp-sized block `sub` of tile `tile`.  The warp walks the
-// tile's list on its own, 32 records at a time, through two shared buffers:
-// while it evaluates chunk k (every lane tests one record against the warp's
-// rectangle, then the records that pass are evaluated by all 32 lanes in list
-// order), the records of chunk k+1 are being copied in, and the entry indices
-// of chunk k+2 are being loaded.  The walk ends as soon as the block's own
-// pixels are done (after the copies in flight have landed).
-template <bool LOSS, bool GEO>
+// tile's list on its own, CH records at a time (the batch: 32 or 64, one or two
+// per lane), through two shared buffers: while it evaluates chunk k (every
+// lane tests its records against the warp's rectangle, then the records that
+// pass are evaluated by all 32 lanes in list order), the records of chunk k+1
+// are being copied in, and the entry indices of chunk k+2 are being loaded.
+// The walk ends as soon as the block's own pixels are done (after the copies
+// in flight have landed).  buf[b][s] is sub-chunk s (32 records) of buffer b.
+template <bool LOSS, bool GEO, int CH>
 __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restrict__ ws, const Layout& L,
-                                const gs_maps& maps, int tile, int sub, float4 (*buf)[4][32], uint32_t& evals,
-                                uint32_t& blended) {
+                                const gs_maps& maps, int tile, int sub, float4 (*buf)[CH / 32][kSlots<LOSS>][32],
+                                uint32_t& evals, uint32_t& blended) {
+  constexpr int NS = CH / 32;   // 32-record sub-chunks per chunk
   const TileCtx c = tile_ctx(fd, tile, sub);
   const int2 range = at<int2>(ws, L.ranges)[tile];
   const uint32_t* pval = at<uint32_t>(ws, L.pval_final);
@@ -213,20 +219,35 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   uint32_t nblend = 0;
   bool done = !c.inside;
   int cur = 0;
-  uint32_t e_next = 0;   // entry of this lane's record in the chunk after the one in flight
+  uint32_t e_next[NS];   // entries of this lane's records in the chunk after the one in flight
+#pragma unroll
+  for (int q = 0; q < NS; ++q) e_next[q] = 0;
   if (range.x < range.y) {
-    if (range.x + lane < range.y) stage_record<LOSS>(buf[0], lane, rec + 4 * (int64_t)__ldg(pval + range.x + lane));
+#pragma unroll
+    for (int q = 0; q < NS; ++q)
+      if (range.x + 32 * q + lane < range.y)
+        stage_record<LOSS>(buf[0][q], lane, rec + 4 * (int64_t)__ldg(pval + range.x + 32 * q + lane));
     cp_async_commit();
-    if (range.x + 32 + lane < range.y) e_next = __ldg(pval + range.x + 32 + lane);
+#pragma unroll
+    for (int q = 0; q < NS; ++q)
+      if (range.x + CH + 32 * q + lane < range.y) e_next[q] = __ldg(pval + range.x + CH + 32 * q + lane);
   }
-  for (int c0 = range.x; c0 < range.y; c0 += 32) {
+  for (int c00 = range.x; c00 < range.y; c00 += CH) {
     if (__all_sync(kFull, done)) break;
-    if (c0 + 32 + lane < range.y) stage_record<LOSS>(buf[cur ^ 1], lane, rec + 4 * (int64_t)e_next);
+#pragma unroll
+    for (int q = 0; q < NS; ++q)
+      if (c00 + CH + 32 * q + lane < range.y) stage_record<LOSS>(buf[cur ^ 1][q], lane, rec + 4 * (int64_t)e_next[q]);
     cp_async_commit();
-    if (c0 + 64 + lane < range.y) e_next = __ldg(pval + c0 + 64 + lane);
-    cp_async_wait<1>();     // this lane's copies of chunk c0 have landed
+#pragma unroll
+    for (int q = 0; q < NS; ++q)
+      if (c00 + 2 * CH + 32 * q + lane < range.y) e_next[q] = __ldg(pval + c00 + 2 * CH + 32 * q + lane);
+    cp_async_wait<1>();     // this lane's copies of chunk c00 have landed
     __syncwarp();           // ... and every lane's are visible
-    float4 (*my)[32] = buf[cur];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+    const int c0 = c00 + 32 * q;
+    if (c0 >= range.y) break;   // past the list: no records and no mask word of this tile
+    float4 (*my)[32] = buf[cur][q];
     const bool rel = c0 + lane < range.y && reaches(my[0][lane], my[1][lane], R, lg_amin);
     unsigned m = __ballot_sync(kFull, rel);
     uint32_t cm = 0;        // records of the chunk this lane blends
@@ -245,7 +266,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       if (Tn < tmin) { done = true; continue; }
       cm |= 1u << j;
       const float w = al * T;
-      const float4 e3 = my[3][j];
+      const float4 e3 = my[kColourSlot<LOSS>][j];
       const float2 w2 = make_float2(w, w);
       if (!GEO) Crg = __ffma2_rn(w2, make_float2(e3.x, e3.y), Crg);
       Cbn = __ffma2_rn(w2, make_float2(e3.z, e3.w), Cbn);   // (b, n0); b is 0 in GEO records
@@ -273,6 +294,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
     if (!GEO) {             // the backward replays only records some lane blended
       const uint32_t wm = __reduce_or_sync(kFull, cm);
       if (lane == 0) cmask[(c0 - range.x) >> 5] = wm;
+    }
     }
     __syncwarp();           // buf[cur] is refilled two chunks later
     cur ^= 1;
@@ -484,7 +506,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       float2 keep[NP], send[NP];
       const bool live = idx <= last;
       // the depth plane (p, z) only for Eq. 23
-      const float4 a = my[0][j], b = my[1][j], e3 = my[3][j];
+      const float4 a = my[0][j], b = my[1][j], e3 = my[kColourSlot<LOSS>][j];
       const float4 e2 = LOSS ? my[2][j] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float2 d = __fadd2_rn(make_float2(a.x, a.y), nfp);     // (dx, dy)
       const float dx = d.x, dy = d.y;
@@ -574,14 +596,22 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
 constexpr int kRenderThreads = 256;
 constexpr int kRenderBlocksPerSm = 3;
 
-template <bool LOSS, bool GEO>
+// The forward's staging buffers: per warp two buffers of CH records in
+// kSlots<LOSS> 16-byte slots (dynamic shared memory, fwd_smem_bytes).
+template <bool LOSS, int CH>
+constexpr size_t fwd_smem_bytes() {
+  return size_t(kRenderThreads / 32) * 2 * CH * kSlots<LOSS> * sizeof(float4);
+}
+
+template <bool LOSS, bool GEO, int CH>
 __global__ void __launch_bounds__(kRenderThreads, kRenderBlocksPerSm)
 k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_maps maps, int subs,
              int n_items) {
-  __shared__ float4 s_rec[kRenderThreads / 32][2][4][32];
+  extern __shared__ __align__(16) float4 s_dyn[];
   Header* hdr = at<Header>(ws, L.hdr);
   if (hdr->status == GS_ERR_CAPACITY) return;
-  float4 (*buf)[4][32] = s_rec[threadIdx.x >> 5];
+  using Buf = float4[CH / 32][kSlots<LOSS>][32];
+  Buf* buf = reinterpret_cast<Buf*>(s_dyn) + 2 * (threadIdx.x >> 5);
   const int* order = at<int>(ws, L.tile_order);
   const int lane = threadIdx.x & 31;
   uint32_t evals = 0, blended = 0;
@@ -590,7 +620,7 @@ k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
     if (lane == 0) item = atomicAdd(&hdr->work_fwd, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= n_items) break;
-    fwd_item<LOSS, GEO>(fd, ws, L, maps, order[item / subs], item % subs, buf, evals, blended);
+    fwd_item<LOSS, GEO, CH>(fd, ws, L, maps, order[item / subs], item % subs, buf, evals, blended);
     __syncwarp();
   }
   count_evals(evals, &hdr->n_evals_fwd);
@@ -601,7 +631,7 @@ template <bool LOSS>
 __global__ void __launch_bounds__(kRenderThreads, kRenderBlocksPerSm)
 k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_map_grads g, int subs,
              int n_items) {
-  __shared__ float4 s_rec[kRenderThreads / 32][4][32];
+  __shared__ float4 s_rec[kRenderThreads / 32][kSlots<LOSS>][32];
   __shared__ uint32_t s_ent[kRenderThreads / 32][32];
   __shared__ __align__(16) float s_red[kRenderThreads / 32][4 * (LOSS ? 4 : 3) * kRedStride];
   Header* hdr = at<Header>(ws, L.hdr);
@@ -625,17 +655,31 @@ k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, g
 
 // A resident wave of blocks for a persistent kernel.
 template <typename K>
-static int persistent_grid(K kernel, int n_items) {
+static int persistent_grid(K kernel, int n_items, size_t smem = 0) {
   int dev = 0, sms = 148, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kRenderThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kRenderThreads, smem);
   const int need = (n_items + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
   // three resident blocks (24 warps) per SM measured fastest for both kernels:
   // a fourth adds issue contention and takes L1 capacity from the record reads
   const int blocks = per_sm < 1 ? 1 : (per_sm < kRenderBlocksPerSm ? per_sm : kRenderBlocksPerSm);
   int g = sms * blocks;
   return g < need ? g : (need < 1 ? 1 : need);
+}
+
+template <bool LOSS, bool GEO, int CH>
+static cudaError_t launch_fwd_variant(const FrameDev* fd, void* ws, const Layout& L, const gs_maps& maps, int subs,
+                                      int n_items, cudaStream_t s) {
+  constexpr size_t smem = fwd_smem_bytes<LOSS, CH>();
+  if (smem > 48 * 1024) {   // above the default dynamic limit: opt in (a host-side attribute)
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_render_fwd<LOSS, GEO, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_render_fwd<LOSS, GEO, CH><<<persistent_grid(k_render_fwd<LOSS, GEO, CH>, n_items, smem), kRenderThreads, smem,
+                                 s>>>(fd, ws, L, maps, subs, n_items);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& hf, const gs_maps& maps,
@@ -647,16 +691,15 @@ cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& hf, con
   if (L.T == 0) return cudaSuccess;
   const int subs = hf.tile_w * hf.tile_h / 32;
   const int n_items = (int)L.T * subs;
+  const bool big = hf.batch == 64;
   if (hf.geometry_only)
-    k_render_fwd<false, true><<<persistent_grid(k_render_fwd<false, true>, n_items), kRenderThreads, 0, s>>>(
-        fd, ws, L, maps, subs, n_items);
-  else if (hf.losses)
-    k_render_fwd<true, false><<<persistent_grid(k_render_fwd<true, false>, n_items), kRenderThreads, 0, s>>>(
-        fd, ws, L, maps, subs, n_items);
-  else
-    k_render_fwd<false, false><<<persistent_grid(k_render_fwd<false, false>, n_items), kRenderThreads, 0,
-                                 s>>>(fd, ws, L, maps, subs, n_items);
-  return cudaGetLastError();
+    return big ? launch_fwd_variant<false, true, 64>(fd, ws, L, maps, subs, n_items, s)
+               : launch_fwd_variant<false, true, 32>(fd, ws, L, maps, subs, n_items, s);
+  if (hf.losses)
+    return big ? launch_fwd_variant<true, false, 64>(fd, ws, L, maps, subs, n_items, s)
+               : launch_fwd_variant<true, false, 32>(fd, ws, L, maps, subs, n_items, s);
+  return big ? launch_fwd_variant<false, false, 64>(fd, ws, L, maps, subs, n_items, s)
+             : launch_fwd_variant<false, false, 32>(fd, ws, L, maps, subs, n_items, s);
 }
 
 __global__ void __launch_bounds__(256)

@@ -91,7 +91,7 @@ struct FrameDev {
   float ext_c;        // float32(2 ln(1/alpha_min))
   int32_t losses;     // per-pixel state of the Eq. 23-24 losses is kept
   int32_t geometry_only;  // forward-only alpha / depth / normal, no backward state
-  int32_t pad_;
+  int32_t batch;      // records a compositing warp stages per round: 32 or 64
 };
 
 // Per-pixel planes of the loss state (each [n_pixels] floats, global pixel

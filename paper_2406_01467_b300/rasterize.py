@@ -31,11 +31,12 @@ class RenderParams:
     clamp_margin: float = 0.15
     losses: bool = False      # keep the per-pixel state of Eq. 23-24 (dist / nloss maps)
     geometry_only: bool = False   # forward-only alpha / depth / normal (no colour, no backward)
+    batch: int = 32           # Gaussians a compositing warp stages per round (32 or 64; performance only)
 
     def to_c(self) -> GsParams:
         return GsParams(self.tile_w, self.tile_h, self.lowpass, self.alpha_min, self.alpha_max,
                         self.T_min, self.median_T, self.clamp_margin, int(bool(self.losses)),
-                        int(bool(self.geometry_only)))
+                        int(bool(self.geometry_only)), int(self.batch))
 
 
 def _ptr(t: Optional[torch.Tensor]):

@@ -74,6 +74,8 @@ def test_workspace_size_grows_with_inputs(lib):
     (lambda f: setattr(f.scenes[0], "sh_degree", 4), "sh_degree"),
     (lambda f: setattr(f.scenes[0], "dtype", 7), "dtype"),
     (lambda f: setattr(f.scenes[0], "means", None), "NULL"),
+    (lambda f: setattr(f.params, "batch", 48), "batch"),
+    (lambda f: setattr(f.params, "batch", 128), "batch"),
 ])
 def test_invalid_arguments_are_rejected_on_the_host(lib, mut, msg):
     f = _frame()

@@ -50,9 +50,11 @@ def test_autotuner_returns_a_candidate_and_caches_it(tmp_path):
     cache = str(tmp_path / "tiles.json")
     cands = ((16, 16), (8, 8), (16, 8))
     p, rep = autotune.tune_tile([st], [(cam, 0)], RenderParams(), candidates=cands, iters=2, cache_path=cache)
-    assert (p.tile_w, p.tile_h) in cands and not rep["cached"] and len(rep["all"]) == 3
+    # every (tile, Gaussians-per-batch) pair is timed
+    assert (p.tile_w, p.tile_h) in cands and p.batch in (32, 64) and not rep["cached"]
+    assert sorted(rep["all"]) == sorted(f"{w}x{h}/b{b}" for w, h in cands for b in (32, 64))
     p2, rep2 = autotune.tune_tile([st], [(cam, 0)], RenderParams(), candidates=cands, cache_path=cache)
-    assert rep2["cached"] and (p2.tile_w, p2.tile_h) == (p.tile_w, p.tile_h)
+    assert rep2["cached"] and (p2.tile_w, p2.tile_h, p2.batch) == (p.tile_w, p.tile_h, p.batch)
 
 
 @pytest.mark.slow

@@ -221,3 +221,37 @@ def test_forward_after_backward_reports_no_backward_evaluations():
     fr.forward()
     st = fr.stats()
     assert st.n_evals_bwd == 0 and st.n_evals_fwd > 0 and st.status == 0
+
+
+@pytest.mark.parametrize("losses, geo", [(False, False), (True, False), (False, True)])
+def test_maps_do_not_depend_on_the_batch(losses, geo):
+    # Gaussians per batch (records a warp stages per round: 32 or 64) is a
+    # performance knob: bit-identical maps and blend masks, on short (tiny) and
+    # long (200K object scene) tile lists, for the plain, the Eq. 23-24 and the
+    # geometry-only forward
+    for sc, cam in ((scenes.tiny_scene(), scenes.tiny_camera()),
+                    (scenes.object_scene(200_000, seed=1), scenes.object_camera(400, 300, 550.0))):
+        outs = []
+        for batch in (32, 64):
+            fr = _frame(sc, cam, RenderParams(batch=batch, losses=losses, geometry_only=geo))
+            o = [t.cpu().numpy() for t in fr.view_maps(0) if t is not None]
+            if losses:
+                o += [t.cpu().numpy() for t in fr.loss_maps(0)]
+            st = fr.stats()
+            o.append(np.array([st.n_evals_fwd, st.n_blended, st.n_pairs]))
+            outs.append(o)
+        for a, b in zip(*outs):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_backward_with_batch_64_matches_oracle():
+    sc, cam = scenes.tiny_scene(), scenes.tiny_camera()
+    p = RenderParams(batch=64, tile_w=32, tile_h=8)
+    op = oracle_params(p)
+    ref_f = oracle.render(sc, cam, op)
+    up = _upstream(cam, 9, ref_f["margin"] < AMBIG_MARGIN)
+    pg, _, sp, _ = oracle_grads_with_spread(sc, cam, up, op)
+    fr = _frame(sc, cam, p)
+    g = fr.backward(*[torch.from_numpy(u).to(DEV) for u in up])[0]
+    torch.cuda.synchronize()
+    assert_grads_close({k: v.cpu().numpy() for k, v in g.items()}, pg, sp, what="batch 64")
