@@ -378,17 +378,27 @@ __device__ inline void fold_store(const float2 (&keep)[NP], const float2 (&send)
 // -> (CC, O); P3 = sd d -> (P0, P1); Q0 = gs dx d -> (CA, CB); Q1 = w (dC2, dN0)
 // -> (B, N0); Q2 = (0, sd) -> (CUT, Z); Q3 = w (dN1, dN2) -> (N1, N2).
 // NP = 3: P0, P1, P2, Q0, Q1 as above; Q2 = w (dN1, dN2) -> (N1, N2); values
-// 12-15 are unused.
+// 12-15 are unused.  Value s is read from row (s & 3) of half s >> 2 for s < 8
+// and from row 4 + (s & 1) of half (s >> 1) & 1 for 8 <= s < 12, so that each
+// group of 8 lanes reads 8 distinct 16-byte bank groups (row r of half q
+// starts at bank group (9 r + 4 q) mod 8).
 constexpr unsigned long long kFoldSlots4 = 0xba76fe329854dc10ull;
-constexpr unsigned long long kFoldSlots3 = 0x6666bafe3254dc10ull;
+constexpr unsigned long long kFoldSlots3 = 0x6666ba54fe32dc10ull;
 
 template <int NP>
 __device__ inline float reduce_rows(const float* __restrict__ red) {
   const int lane = threadIdx.x & 31, s = lane & 15;
   if (s >= 4 * NP) return 0.f;
-  const int q = s >= 2 * NP;   // the Q half of the row
+  int q, row;   // the half (P or Q) and the row of value s
+  if (NP == 4) {
+    q = s >> 3;
+    row = s & 7;
+  } else {
+    q = s < 8 ? s >> 2 : (s >> 1) & 1;
+    row = s < 8 ? s & 3 : 4 + (s & 1);
+  }
   const float4* r =
-      reinterpret_cast<const float4*>(red + ((lane >> 4) * 2 * NP + s - q * 2 * NP) * kRedStride + q * 16);
+      reinterpret_cast<const float4*>(red + ((lane >> 4) * 2 * NP + row) * kRedStride + q * 16);
   float2 h[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
