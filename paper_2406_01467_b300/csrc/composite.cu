@@ -251,21 +251,19 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
     const bool rel = c0 + lane < range.y && reaches(my[0][lane], my[1][lane], R, lg_amin);
     unsigned m = __ballot_sync(kFull, rel);
     uint32_t cm = 0;        // records of the chunk this lane blends
-    while (m) {
-      const int j = __ffs(m) - 1;
-      m &= m - 1;
-      if (done) continue;
-      ++evals;
-      const float4 a = my[0][j], b = my[1][j];
-      const float2 d = __fadd2_rn(make_float2(a.x, a.y), nfp);   // (dx, dy)
-      const float dx = d.x, dy = d.y;
-      const float sl = splat_s(a.z, a.w, b.x, d, __fmul2_rn(d, d));
-      const float al = fminf(amax, __fmul_rn(b.y, ex2(-sl)));
-      if (al < amin) continue;
-      const float Tn = T * (1.f - al);
-      if (Tn < tmin) { done = true; continue; }
-      cm |= 1u << j;
-      const float w = al * T;
+    // Two records per round: both alphas are computed before the blends (the
+    // chain through T is the only serial part).  Branch-free: a lane that is
+    // done, whose alpha misses the cut, or whose transmittance would fall below
+    // T_min blends with alpha 0, which leaves every sum and T exactly as they
+    // were (w = 0 adds +/-0).
+    auto blend_one = [&](int j, bool valid, float al0, float4 b, float2 d) {
+      evals += valid && !done;
+      const float Tn = T * (1.f - al0);
+      const bool hit = valid && !done && al0 >= amin;
+      const bool bl = hit && Tn >= tmin;
+      done = done || (hit && !bl);
+      cm |= static_cast<uint32_t>(bl) << j;
+      const float w = bl ? al0 * T : 0.f;
       const float4 e3 = my[kColourSlot<LOSS>][j];
       const float2 w2 = make_float2(w, w);
       if (!GEO) Crg = __ffma2_rn(w2, make_float2(e3.x, e3.y), Crg);
@@ -276,19 +274,35 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       float dk = 0.f;
       if (LOSS) {
         const float4 e2 = my[2][j];
-        dk = e2.z + e2.x * dx + e2.y * dy;
-        if (last < 0) d0 = dk;
+        dk = e2.z + e2.x * d.x + e2.y * d.y;
+        if (bl && last < 0) d0 = dk;
         const float sd = dk - d0;
         Ws += w;
         S1 += w * sd;
         S2 += w * sd * sd;
       }
-      if (med < 0 && Tn <= tmed) {
+      if (bl && med < 0 && Tn <= tmed) {
         med = c0 + j;
         if (LOSS) depth = dk;
       }
-      last = c0 + j;
-      T = Tn;
+      if (bl) {
+        last = c0 + j;
+        T = Tn;
+      }
+    };
+    while (m) {
+      const int jA = __ffs(m) - 1;
+      m &= m - 1;
+      const bool two = m != 0;
+      const int jB = two ? __ffs(m) - 1 : jA;
+      m &= m - 1;
+      const float4 aA = my[0][jA], bA = my[1][jA], aB = my[0][jB], bB = my[1][jB];
+      const float2 dA = __fadd2_rn(make_float2(aA.x, aA.y), nfp);   // (dx, dy)
+      const float2 dB = __fadd2_rn(make_float2(aB.x, aB.y), nfp);
+      const float alA = fminf(amax, __fmul_rn(bA.y, ex2(-splat_s(aA.z, aA.w, bA.x, dA, __fmul2_rn(dA, dA)))));
+      const float alB = fminf(amax, __fmul_rn(bB.y, ex2(-splat_s(aB.z, aB.w, bB.x, dB, __fmul2_rn(dB, dB)))));
+      blend_one(jA, true, alA, bA, dA);
+      blend_one(jB, two, alB, bB, dB);
     }
     nblend += __popc(cm);
     if (!GEO) {             // the backward replays only records some lane blended
