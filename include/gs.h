@@ -183,7 +183,9 @@ typedef struct {
   int64_t n_visible;    /* entries that touch at least one pixel */
   int64_t n_pairs;      /* (tile, Gaussian) pairs needed */
   int64_t n_nonfinite;  /* entries culled for non-finite inputs */
-  int64_t n_evals_fwd;  /* (pixel, splat) evaluations of the last gs_render_fwd */
+  int64_t n_evals_fwd;  /* (pixel, splat) pairs tested by the last gs_render_fwd: the splats
+                           that pass the pixel's 8x4 block test, in every 32-splat chunk of
+                           the tile list that the pixel enters unfinished */
   int64_t n_evals_bwd;  /* (pixel, splat) evaluations of the last gs_composite_bwd */
   int64_t n_blended;    /* (pixel, splat) pairs blended (Eq. 3) by the last gs_render_fwd */
   int32_t status;       /* sticky gs_status of the device work */

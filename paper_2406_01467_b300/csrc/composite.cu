@@ -257,7 +257,6 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
     // T_min blends with alpha 0, which leaves every sum and T exactly as they
     // were (w = 0 adds +/-0).
     auto blend_one = [&](int j, bool valid, float al0, float4 b, float2 d) {
-      evals += valid && !done;
       const float Tn = T * (1.f - al0);
       const bool hit = valid && !done && al0 >= amin;
       const bool bl = hit && Tn >= tmin;
@@ -290,6 +289,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
         T = Tn;
       }
     };
+    if (!done) evals += __popc(m);
     while (m) {
       const int jA = __ffs(m) - 1;
       m &= m - 1;
