@@ -256,9 +256,9 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
     // done, whose alpha misses the cut, or whose transmittance would fall below
     // T_min blends with alpha 0, which leaves every sum and T exactly as they
     // were (w = 0 adds +/-0).
-    auto blend_one = [&](int j, bool valid, float al0, float4 b, float2 d) {
+    auto blend_one = [&](int j, float al0, float4 b, float2 d) {
       const float Tn = T * (1.f - al0);
-      const bool hit = valid && !done && al0 >= amin;
+      const bool hit = !done && al0 >= amin;
       const bool bl = hit && Tn >= tmin;
       done = done || (hit && !bl);
       cm |= static_cast<uint32_t>(bl) << j;
@@ -290,19 +290,29 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
       }
     };
     if (!done) evals += __popc(m);
-    while (m) {
+    auto alpha_of = [&](int j, float4& b, float2& d) {
+      const float4 a = my[0][j];
+      b = my[1][j];
+      d = __fadd2_rn(make_float2(a.x, a.y), nfp);   // (dx, dy)
+      return fminf(amax, __fmul_rn(b.y, ex2(-splat_s(a.z, a.w, b.x, d, __fmul2_rn(d, d)))));
+    };
+    while (m & (m - 1)) {   // two or more records left
       const int jA = __ffs(m) - 1;
       m &= m - 1;
-      const bool two = m != 0;
-      const int jB = two ? __ffs(m) - 1 : jA;
+      const int jB = __ffs(m) - 1;
       m &= m - 1;
-      const float4 aA = my[0][jA], bA = my[1][jA], aB = my[0][jB], bB = my[1][jB];
-      const float2 dA = __fadd2_rn(make_float2(aA.x, aA.y), nfp);   // (dx, dy)
-      const float2 dB = __fadd2_rn(make_float2(aB.x, aB.y), nfp);
-      const float alA = fminf(amax, __fmul_rn(bA.y, ex2(-splat_s(aA.z, aA.w, bA.x, dA, __fmul2_rn(dA, dA)))));
-      const float alB = fminf(amax, __fmul_rn(bB.y, ex2(-splat_s(aB.z, aB.w, bB.x, dB, __fmul2_rn(dB, dB)))));
-      blend_one(jA, true, alA, bA, dA);
-      blend_one(jB, two, alB, bB, dB);
+      float4 bA, bB;
+      float2 dA, dB;
+      const float alA = alpha_of(jA, bA, dA), alB = alpha_of(jB, bB, dB);
+      blend_one(jA, alA, bA, dA);
+      blend_one(jB, alB, bB, dB);
+    }
+    if (m) {
+      const int j = __ffs(m) - 1;
+      float4 b;
+      float2 d;
+      const float al = alpha_of(j, b, d);
+      blend_one(j, al, b, d);
     }
     nblend += __popc(cm);
     if (!GEO) {             // the backward replays only records some lane blended
