@@ -22,7 +22,7 @@ def evaluated_in(dtype):
     A test instrument only: the FP64 results are the reference.  The same
     definition evaluated in FP32 shows how far FP32 rounding alone moves each
     result, which is the scale against which an FP32 implementation's
-    differences from the FP64 values are judged entry by entry.  The binning
+    differences from the FP64 values are weighed entry by entry.  The binning
     decisions are FP32 either way."""
     from . import appearance, losses
     mods = (gaussians, comp, losses, appearance, sys.modules[__name__])
