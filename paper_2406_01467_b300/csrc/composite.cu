@@ -251,8 +251,9 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
     const bool rel = c0 + lane < range.y && reaches(my[0][lane], my[1][lane], R, lg_amin);
     unsigned m = __ballot_sync(kFull, rel);
     uint32_t cm = 0;        // records of the chunk this lane blends
-    // Two records per round: both alphas are computed before the blends (the
-    // chain through T is the only serial part).  Branch-free: a lane that is
+    // Two records per round, the odd one alone: both alphas are computed
+    // before the blends (the chain through T is the only serial part).
+    // Branch-free: a lane that is
     // done, whose alpha misses the cut, or whose transmittance would fall below
     // T_min blends with alpha 0, which leaves every sum and T exactly as they
     // were (w = 0 adds +/-0).
@@ -289,6 +290,8 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
         T = Tn;
       }
     };
+    // tested pairs: the records that pass the block test, for a pixel still
+    // unfinished at the chunk's start
     if (!done) evals += __popc(m);
     auto alpha_of = [&](int j, float4& b, float2& d) {
       const float4 a = my[0][j];
