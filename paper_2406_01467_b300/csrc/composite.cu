@@ -514,14 +514,26 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
   // the forward's per-chunk masks name the records some lane of this block
   // blended; the others have zero gradient here and are not replayed
   const uint32_t* cmask = at<uint32_t>(ws, L.cmask) + (int64_t)sub * L.cmask_words + (range.x >> 5) + tile;
-  for (int k = wmax >= range.x ? (wmax - range.x) >> 5 : -1; k >= 0; --k) {
-    const uint32_t wm = cmask[k];
+  // the mask word and this lane's entry of the next chunk are loaded one chunk
+  // ahead, so a chunk's staging waits for one round trip to L2, not three
+  const int k_first = wmax >= range.x ? (wmax - range.x) >> 5 : -1;
+  uint32_t wm_next = 0, e_next = 0;
+  if (k_first >= 0) {
+    wm_next = cmask[k_first];
+    const int c = range.x + 32 * k_first + lane;
+    e_next = c < range.y ? pval[c] : 0u;
+  }
+  for (int k = k_first; k >= 0; --k) {
+    const uint32_t wm = wm_next, e_cur = e_next;
+    if (k > 0) {
+      wm_next = cmask[k - 1];
+      e_next = pval[range.x + 32 * (k - 1) + lane];   // a full chunk: every chunk but the last is
+    }
     if (wm == 0) continue;
     const int c0 = range.x + 32 * k;
     if ((wm >> lane) & 1u) {   // copies straight to shared memory, no registers
-      const uint32_t e = pval[c0 + lane];
-      stage_record<LOSS, false>(my, lane, rec + 4 * (int64_t)e);
-      my_e[lane] = e;
+      stage_record<LOSS, false>(my, lane, rec + 4 * (int64_t)e_cur);
+      my_e[lane] = e_cur;
     }
     cp_async_commit();
     cp_async_wait<0>();
