@@ -215,6 +215,8 @@ static gs_status prepare_ws(const gs_frame* f, FrameDev& fd, Layout& L) {
 // addresses serialise, so the unused view and scene slots (most of the 11 KB)
 // are left out; no kernel reads them.
 __global__ void k_setup(FrameDev fd, FrameDev* dst, Header* hdr, BwdCounters* bc) {
+  pdl_wait();
+  pdl_trigger();
   const uint32_t* src = reinterpret_cast<const uint32_t*>(&fd);
   uint32_t* d = reinterpret_cast<uint32_t*>(dst);
   const int nv = fd.n_views, ns = fd.n_scenes;
@@ -244,7 +246,7 @@ static_assert(sizeof(ViewDev) % 4 == 0 && sizeof(SceneDev) % 4 == 0 && offsetof(
 static_assert(sizeof(Header) == 256, "Header is one 256-byte block");
 
 cudaError_t launch_setup(const FrameDev& fd, void* ws, const Layout& L, cudaStream_t s) {
-  k_setup<<<1, 256, 0, s>>>(fd, at<FrameDev>(ws, L.frame), at<Header>(ws, L.hdr),
+  launch_pdl(k_setup, 1, 256, 0, s, fd, at<FrameDev>(ws, L.frame), at<Header>(ws, L.hdr),
                             fd.geometry_only ? nullptr : at<BwdCounters>(ws, L.bwdcnt));
   return cudaGetLastError();
 }

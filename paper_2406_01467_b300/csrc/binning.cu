@@ -193,6 +193,8 @@ __global__ void __launch_bounds__(kSortThreads)
 k_compact(const uint32_t* __restrict__ key, int64_t E, uint32_t* __restrict__ okey, uint32_t* __restrict__ oval,
           uint32_t* __restrict__ ghist, unsigned long long* __restrict__ words, int* ticket,
           unsigned long long* __restrict__ n_vis_out, Header* hdr) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t s_wtot[8];
   __shared__ uint32_t s_h[kMaxPasses][kRadix];   // the depth sort's digit histograms
   __shared__ int s_tk;
@@ -240,6 +242,8 @@ k_pair_offsets(const uint32_t* __restrict__ sval, const unsigned long long* n_vi
                const uint32_t* __restrict__ touched, uint32_t* __restrict__ pair_off,
                uint32_t* __restrict__ chunk_first, int64_t n_chunks, unsigned long long* __restrict__ words,
                int* ticket, unsigned long long* __restrict__ n_pairs_out, int64_t cap, Header* hdr) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t s_wtot[8];
   __shared__ int s_tk;
   __shared__ unsigned long long s_excl;
@@ -321,6 +325,8 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
        const short4* __restrict__ rect, const uint32_t* __restrict__ pair_off, int64_t cap,
        uint32_t* __restrict__ ptile, uint32_t* __restrict__ pval, const uint32_t* __restrict__ chunk_first,
        int64_t n_chunks, int tile_passes, uint32_t* __restrict__ ghist) {
+  pdl_wait();
+  pdl_trigger();
   // per entry of the slice: its first pair, and (entry, first tile of its
   // rectangle, rectangle width | tile row length << 16, 1 / width)
   __shared__ uint32_t s_off[kEmitChunk + 1];
@@ -424,6 +430,8 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
 __global__ void __launch_bounds__(256)
 k_ranges(const uint32_t* __restrict__ ptile, const unsigned long long* n_pairs_ptr, int64_t cap,
          int2* __restrict__ ranges) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t P = clamp_count(n_pairs_ptr, cap);
   // four consecutive pairs per thread: one 16-byte load (the buffer is 16-byte
   // aligned), scalar loads for its two neighbours and for a ragged tail
@@ -464,6 +472,8 @@ __device__ inline int cost_bucket(uint32_t c) {
 __global__ void __launch_bounds__(1024) k_tile_order(const int2* __restrict__ ranges,
                                                      const uint32_t* __restrict__ cost, int T,
                                                      int* __restrict__ order) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int cnt[256];
   for (int b = threadIdx.x; b < 256; b += blockDim.x) cnt[b] = 0;
   __syncthreads();
@@ -494,7 +504,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(const int2* __restrict__ ra
 }
 
 cudaError_t launch_tile_order(void* ws, const Layout& L, const uint32_t* cost, int* order, cudaStream_t s) {
-  if (L.T > 0) k_tile_order<<<1, 1024, 0, s>>>(at<int2>(ws, L.ranges), cost, (int)L.T, order);
+  if (L.T > 0) launch_pdl(k_tile_order, 1, 1024, 0, s, at<int2>(ws, L.ranges), cost, (int)L.T, order);
   return cudaGetLastError();
 }
 
@@ -560,6 +570,8 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
 k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
            uint32_t* __restrict__ vout, const unsigned long long* count_ptr, int64_t cap, int pass, int dbits,
            const uint32_t* __restrict__ ghist, unsigned long long* __restrict__ look, int* ticket, Header* hdr) {
+  pdl_wait();
+  pdl_trigger();
   // [half][warp][digit] running digit counts of a warp's two halves of items
   // (rounds 0-7 and 8-15: two independent chains), then [0]: the warps' bases
   __shared__ uint16_t s_wc[2][8][kRadix];
@@ -695,9 +707,9 @@ static cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t
     const int dbits = bits - kRadixBits * p < kRadixBits ? bits - kRadixBits * p : kRadixBits;
     unsigned long long* lp = look + (int64_t)p * nb * kRadix;
     if (dbits == kRadixBits)
-      k_onesweep<2, true><<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, cap, p, dbits, ghist, lp, tickets + p, hdr);
+      launch_pdl(k_onesweep<2, true>, nb, kSortThreads, 0, s, ki, vi, ko, vo, count, cap, p, dbits, ghist, lp, tickets + p, hdr);
     else
-      k_onesweep<3, false><<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, cap, p, dbits, ghist, lp, tickets + p, hdr);
+      launch_pdl(k_onesweep<3, false>, nb, kSortThreads, 0, s, ki, vi, ko, vo, count, cap, p, dbits, ghist, lp, tickets + p, hdr);
     uint32_t* t;
     t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
@@ -728,7 +740,7 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   cudaError_t e0 = cudaMemsetAsync(at<char>(ws, L.sortaux[0]), 0, L.ranges + 8 * (size_t)L.T - L.sortaux[0], s);
   if (e0 != cudaSuccess) return e0;
   // 1. compaction (also counts the depth keys' digits for the sort)
-  k_compact<<<L.nb_E, kSortThreads, 0, s>>>(key, L.E, vk0, vv0, at<uint32_t>(ws, L.sortaux[0]), scan_words,
+  launch_pdl(k_compact, L.nb_E, kSortThreads, 0, s, key, L.E, vk0, vv0, at<uint32_t>(ws, L.sortaux[0]), scan_words,
                                            scan_ticket, &hdr->n_vis, hdr);
   // 2. depth sort: 31 bits (z > 0, so the sign bit is clear)
   cudaError_t err = radix_sort(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, at<void>(ws, L.sortaux[0]),
@@ -738,7 +750,7 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   uint32_t* pair_off = at<uint32_t>(ws, L.pair_off);
   uint32_t* chunk_first = at<uint32_t>(ws, L.chunk_first);
   const int64_t n_chunks = (L.Pcap + kEmitChunk - 1) / kEmitChunk + 1;
-  k_pair_offsets<<<L.nb_E, kSortThreads, 0, s>>>(vv0, &hdr->n_vis, L.E, touched, pair_off, chunk_first, n_chunks,
+  launch_pdl(k_pair_offsets, L.nb_E, kSortThreads, 0, s, vv0, &hdr->n_vis, L.E, touched, pair_off, chunk_first, n_chunks,
                                                   scan_words + L.nb_E, scan_ticket + 1, &hdr->n_pairs, L.Pcap,
                                                   hdr);
   // 4. emission
@@ -746,7 +758,7 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   const int bits = tile_sort_bits(L.T);
   const int tile_passes = (bits + kRadixBits - 1) / kRadixBits;
   const int eg = (int)std::min<int64_t>((L.Pcap + kEmitChunk - 1) / kEmitChunk, 148 * 8);
-  k_emit<<<eg, kSortThreads, 0, s>>>(fd, vv0, &hdr->n_vis, &hdr->n_pairs, L.E, at<short4>(ws, L.rect),
+  launch_pdl(k_emit, eg, kSortThreads, 0, s, fd, vv0, &hdr->n_vis, &hdr->n_pairs, L.E, at<short4>(ws, L.rect),
                                      pair_off, L.Pcap, pt0, pv0, chunk_first, n_chunks, tile_passes,
                                      at<uint32_t>(ws, L.sortaux[1]));
   // 5. tile sort
@@ -756,7 +768,7 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   uint32_t* ptile = at<uint32_t>(ws, L.ptile_final);
   // 6. ranges
   int g = (int)std::max<int64_t>(1, std::min<int64_t>((L.Pcap / 4 + 255) / 256, 148 * 16));
-  k_ranges<<<g, 256, 0, s>>>(ptile, &hdr->n_pairs, L.Pcap, at<int2>(ws, L.ranges));
+  launch_pdl(k_ranges, g, 256, 0, s, ptile, &hdr->n_pairs, L.Pcap, at<int2>(ws, L.ranges));
   // 7. compositing work order (by list length)
   return launch_tile_order(ws, L, nullptr, at<int>(ws, L.tile_order), s);
 }

@@ -656,6 +656,8 @@ template <bool LOSS, bool GEO, int CH>
 __global__ void __launch_bounds__(kRenderThreads, kRenderBlocksPerSm)
 k_render_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_maps maps, int subs,
              int n_items) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) float4 s_dyn[];
   Header* hdr = at<Header>(ws, L.hdr);
   if (hdr->status == GS_ERR_CAPACITY) return;
@@ -680,6 +682,8 @@ template <bool LOSS>
 __global__ void __launch_bounds__(kRenderThreads, kRenderBlocksPerSm)
 k_render_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, gs_map_grads g, int subs,
              int n_items) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float4 s_rec[kRenderThreads / 32][kSlots<LOSS>][32];
   __shared__ uint32_t s_ent[kRenderThreads / 32][32];
   __shared__ __align__(16) float s_red[kRenderThreads / 32][4 * (LOSS ? 4 : 3) * kRedStride];
@@ -726,8 +730,7 @@ static cudaError_t launch_fwd_variant(const FrameDev* fd, void* ws, const Layout
         cudaFuncSetAttribute(k_render_fwd<LOSS, GEO, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_render_fwd<LOSS, GEO, CH><<<persistent_grid(k_render_fwd<LOSS, GEO, CH>, n_items, smem), kRenderThreads, smem,
-                                 s>>>(fd, ws, L, maps, subs, n_items);
+  launch_pdl(k_render_fwd<LOSS, GEO, CH>, persistent_grid(k_render_fwd<LOSS, GEO, CH>, n_items, smem), kRenderThreads, smem, s, fd, ws, L, maps, subs, n_items);
   return cudaGetLastError();
 }
 
@@ -754,6 +757,8 @@ cudaError_t launch_render_fwd(void* ws, const Layout& L, const FrameDev& hf, con
 __global__ void __launch_bounds__(256)
 k_bwd_clear(const uint32_t* __restrict__ vis, const unsigned long long* n_vis_ptr, int64_t E,
             float4* __restrict__ grad2d, BwdCounters* bc) {
+  pdl_wait();
+  pdl_trigger();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     bc->n_evals_bwd = 0;
     bc->work_bwd = 0;
@@ -772,7 +777,7 @@ cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& hf, con
   // backward reads), 4 threads per 64-byte row
   {
     const int g = (int)std::min<int64_t>(std::max<int64_t>((4 * L.E + 255) / 256, 1), 148 * 16);
-    k_bwd_clear<<<g, 256, 0, s>>>(at<uint32_t>(ws, L.vval[0]), &hdr->n_vis, L.E, at<float4>(ws, L.grad2d),
+    launch_pdl(k_bwd_clear, g, 256, 0, s, at<uint32_t>(ws, L.vval[0]), &hdr->n_vis, L.E, at<float4>(ws, L.grad2d),
                                   at<BwdCounters>(ws, L.bwdcnt));
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
@@ -781,11 +786,9 @@ cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& hf, con
   const int subs = hf.tile_w * hf.tile_h / 32;
   const int n_items = (int)L.T * subs;
   if (hf.losses && (g.ddist || g.dnloss))
-    k_render_bwd<true><<<persistent_grid(k_render_bwd<true>, n_items), kRenderThreads, 0, s>>>(
-        fd, ws, L, g, subs, n_items);
+    launch_pdl(k_render_bwd<true>, persistent_grid(k_render_bwd<true>, n_items), kRenderThreads, 0, s, fd, ws, L, g, subs, n_items);
   else
-    k_render_bwd<false><<<persistent_grid(k_render_bwd<false>, n_items), kRenderThreads, 0, s>>>(
-        fd, ws, L, g, subs, n_items);
+    launch_pdl(k_render_bwd<false>, persistent_grid(k_render_bwd<false>, n_items), kRenderThreads, 0, s, fd, ws, L, g, subs, n_items);
   return cudaGetLastError();
 }
 

@@ -75,6 +75,8 @@ __device__ inline int block_view(const LossGrid& G, int n_views, int b) {
 // Forward: one thread per pixel, neighbours read through the cache.
 __global__ void __launch_bounds__(kLX * kLY)
 k_nloss_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, LossGrid G, float* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   if (at<Header>(ws, L.hdr)->status == GS_ERR_CAPACITY) return;   // nothing was rendered
   const int v = block_view(G, fd->n_views, blockIdx.x);
   const ViewDev& V = fd->views[v];
@@ -109,6 +111,8 @@ k_nloss_fwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, Lo
 __global__ void __launch_bounds__(kLX * kLY)
 k_nloss_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, LossGrid G,
             const float* __restrict__ gin) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float sD[kDY][kDX];
   __shared__ unsigned char sA[kDY][kDX];
   __shared__ float sG[kCY][kCX][6];   // da, db of each centre (0 where n~ is undefined)
@@ -217,7 +221,7 @@ cudaError_t launch_nloss_fwd(void* ws, const Layout& L, const FrameDev& hf, floa
   int nb = 0;
   const LossGrid G = loss_grid(hf, nb);
   if (nb == 0) return cudaSuccess;
-  k_nloss_fwd<<<nb, kLX * kLY, 0, s>>>(at<FrameDev>(ws, L.frame), ws, L, G, nloss);
+  launch_pdl(k_nloss_fwd, nb, kLX * kLY, 0, s, at<FrameDev>(ws, L.frame), ws, L, G, nloss);
   return cudaGetLastError();
 }
 
@@ -226,7 +230,7 @@ cudaError_t launch_nloss_bwd(void* ws, const Layout& L, const FrameDev& hf, cons
   int nb = 0;
   const LossGrid G = loss_grid(hf, nb);
   if (nb == 0) return cudaSuccess;
-  k_nloss_bwd<<<nb, kLX * kLY, 0, s>>>(at<FrameDev>(ws, L.frame), ws, L, G, dnloss);
+  launch_pdl(k_nloss_bwd, nb, kLX * kLY, 0, s, at<FrameDev>(ws, L.frame), ws, L, G, dnloss);
   return cudaGetLastError();
 }
 

@@ -272,6 +272,8 @@ __device__ inline void load_sh(const SceneDev& S, int64_t g, float* c) {
 template <typename T, int D, bool GEO>
 __global__ void __launch_bounds__(kPreThreads, 5)
 k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int K = (D + 1) * (D + 1);
   Header* hdr = at<Header>(ws, L.hdr);
   float4* rec = at<float4>(ws, L.rec);
@@ -457,6 +459,8 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
 template <typename T, int D, bool FILT>
 __global__ void __launch_bounds__(kPreThreads, 5)
 k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L, GradPtrs gp) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int K = (D + 1) * (D + 1);
   const uint32_t* key = at<uint32_t>(ws, L.key);
   const float4* g2d = at<float4>(ws, L.grad2d);
@@ -763,10 +767,10 @@ static int grid_chunks(int n_chunks) {
 template <typename T>
 static cudaError_t fwd_t(int deg, const FrameDev* fd, void* ws, const Layout& L, int grid, cudaStream_t s) {
   switch (deg) {
-    case 0: k_preprocess<T, 0, false><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
-    case 1: k_preprocess<T, 1, false><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
-    case 2: k_preprocess<T, 2, false><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
-    default: k_preprocess<T, 3, false><<<grid, kPreThreads, 0, s>>>(fd, ws, L); break;
+    case 0: launch_pdl(k_preprocess<T, 0, false>, grid, kPreThreads, 0, s, fd, ws, L); break;
+    case 1: launch_pdl(k_preprocess<T, 1, false>, grid, kPreThreads, 0, s, fd, ws, L); break;
+    case 2: launch_pdl(k_preprocess<T, 2, false>, grid, kPreThreads, 0, s, fd, ws, L); break;
+    default: launch_pdl(k_preprocess<T, 3, false>, grid, kPreThreads, 0, s, fd, ws, L); break;
   }
   return cudaGetLastError();
 }
@@ -775,10 +779,10 @@ template <typename T, bool FILT>
 static cudaError_t bwd_t(int deg, const FrameDev* fd, void* ws, const Layout& L, const GradPtrs& gp, int grid,
                          cudaStream_t s) {
   switch (deg) {
-    case 0: k_preprocess_bwd<T, 0, FILT><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
-    case 1: k_preprocess_bwd<T, 1, FILT><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
-    case 2: k_preprocess_bwd<T, 2, FILT><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
-    default: k_preprocess_bwd<T, 3, FILT><<<grid, kPreThreads, 0, s>>>(fd, ws, L, gp); break;
+    case 0: launch_pdl(k_preprocess_bwd<T, 0, FILT>, grid, kPreThreads, 0, s, fd, ws, L, gp); break;
+    case 1: launch_pdl(k_preprocess_bwd<T, 1, FILT>, grid, kPreThreads, 0, s, fd, ws, L, gp); break;
+    case 2: launch_pdl(k_preprocess_bwd<T, 2, FILT>, grid, kPreThreads, 0, s, fd, ws, L, gp); break;
+    default: launch_pdl(k_preprocess_bwd<T, 3, FILT>, grid, kPreThreads, 0, s, fd, ws, L, gp); break;
   }
   return cudaGetLastError();
 }
@@ -801,8 +805,8 @@ cudaError_t launch_preprocess(void* ws, const Layout& L, const FrameDev& hf, cud
   const int grid = grid_chunks(hf.n_chunks);
   cudaError_t e = cudaSuccess;
   if (hf.geometry_only) {   // one launch per dtype, SH not read
-    if (k & (0xFu << (4 * GS_F32))) k_preprocess<float, 0, true><<<grid, kPreThreads, 0, s>>>(fd, ws, L);
-    if (k & (0xFu << (4 * GS_BF16))) k_preprocess<__nv_bfloat16, 0, true><<<grid, kPreThreads, 0, s>>>(fd, ws, L);
+    if (k & (0xFu << (4 * GS_F32))) launch_pdl(k_preprocess<float, 0, true>, grid, kPreThreads, 0, s, fd, ws, L);
+    if (k & (0xFu << (4 * GS_BF16))) launch_pdl(k_preprocess<__nv_bfloat16, 0, true>, grid, kPreThreads, 0, s, fd, ws, L);
     return cudaGetLastError();
   }
   for (int deg = 0; deg < 4 && e == cudaSuccess; ++deg) {
