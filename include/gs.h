@@ -29,6 +29,11 @@
  * a gs_preprocess / gs_bin / gs_render_fwd / gs_render_bwd sequence can be
  * captured in a CUDA graph.  Device-side problems (pair capacity exceeded,
  * non-finite inputs) set a sticky word inside the workspace that gs_check reads.
+ * The kernels are launched with programmatic dependent launch: each waits for
+ * the work before it in the stream to complete before it touches memory, and
+ * lets the next kernel be scheduled early.  A caller's kernel that follows them
+ * with that launch attribute must itself wait (cudaGridDependencySynchronize)
+ * before it reads their outputs; ordinary launches need nothing.
  *
  * Errors: argument errors are detected on the host and returned at once
  * (GS_ERR_INVALID_ARG, nothing is enqueued); a failed launch returns
