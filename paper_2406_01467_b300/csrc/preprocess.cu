@@ -382,6 +382,18 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
 #pragma unroll
         for (int j = 0; j < 3 * K; ++j) shchk += c[j] * 0.f;
         if (shchk != 0.f) { valid = false; ++nonfinite; }
+        // the colour at once, so the SH registers are free before the geometry
+        float d[3] = {m[0] - V.campos[0], m[1] - V.campos[1], m[2] - V.campos[2]};
+        float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        float Y[16];
+        sh_basis(d[0] * il, d[1] * il, d[2] * il, Y);
+#pragma unroll
+        for (int ch3 = 0; ch3 < 3; ++ch3) {
+          float acc = 0.5f;
+#pragma unroll
+          for (int j = 0; j < K; ++j) acc += Y[j] * c[3 * j + ch3];
+          rgb[ch3] = fmaxf(acc, 0.f);
+        }
       }
       const float tc = sqrtf(xc[0] * xc[0] + xc[1] * xc[1] + xc[2] * xc[2]);
       const float it = 1.f / tc;
@@ -413,19 +425,6 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
       nn[0] = mv0 * im; nn[1] = mv1 * im; nn[2] = mv2 * im;
       valid = valid && (det > 0.f) && isfinite(conic[0]) && isfinite(conic[1]) && isfinite(conic[2]) &&
               isfinite(pp[0]) && isfinite(pp[1]) && isfinite(nn[0]) && isfinite(nn[1]) && isfinite(nn[2]);
-      if constexpr (!GEO) {
-        float d[3] = {m[0] - V.campos[0], m[1] - V.campos[1], m[2] - V.campos[2]};
-        float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        float Y[16];
-        sh_basis(d[0] * il, d[1] * il, d[2] * il, Y);
-#pragma unroll
-        for (int ch3 = 0; ch3 < 3; ++ch3) {
-          float acc = 0.5f;
-#pragma unroll
-          for (int j = 0; j < K; ++j) acc += Y[j] * c[3 * j + ch3];
-          rgb[ch3] = fmaxf(acc, 0.f);
-        }
-      }
     }
     if (valid) {
       float4* r = rec + 4 * e;
