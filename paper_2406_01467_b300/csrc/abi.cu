@@ -247,7 +247,7 @@ static_assert(sizeof(Header) == 256, "Header is one 256-byte block");
 
 cudaError_t launch_setup(const FrameDev& fd, void* ws, const Layout& L, cudaStream_t s) {
   launch_pdl(k_setup, 1, 256, 0, s, fd, at<FrameDev>(ws, L.frame), at<Header>(ws, L.hdr),
-                            fd.geometry_only ? nullptr : at<BwdCounters>(ws, L.bwdcnt));
+             fd.geometry_only ? nullptr : at<BwdCounters>(ws, L.bwdcnt));
   return cudaGetLastError();
 }
 

@@ -707,9 +707,11 @@ static cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t
     const int dbits = bits - kRadixBits * p < kRadixBits ? bits - kRadixBits * p : kRadixBits;
     unsigned long long* lp = look + (int64_t)p * nb * kRadix;
     if (dbits == kRadixBits)
-      launch_pdl(k_onesweep<2, true>, nb, kSortThreads, 0, s, ki, vi, ko, vo, count, cap, p, dbits, ghist, lp, tickets + p, hdr);
+      launch_pdl(k_onesweep<2, true>, nb, kSortThreads, 0, s, ki, vi, ko, vo, count, cap, p, dbits, ghist, lp,
+                 tickets + p, hdr);
     else
-      launch_pdl(k_onesweep<3, false>, nb, kSortThreads, 0, s, ki, vi, ko, vo, count, cap, p, dbits, ghist, lp, tickets + p, hdr);
+      launch_pdl(k_onesweep<3, false>, nb, kSortThreads, 0, s, ki, vi, ko, vo, count, cap, p, dbits, ghist, lp,
+                 tickets + p, hdr);
     uint32_t* t;
     t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
@@ -741,7 +743,7 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   if (e0 != cudaSuccess) return e0;
   // 1. compaction (also counts the depth keys' digits for the sort)
   launch_pdl(k_compact, L.nb_E, kSortThreads, 0, s, key, L.E, vk0, vv0, at<uint32_t>(ws, L.sortaux[0]), scan_words,
-                                           scan_ticket, &hdr->n_vis, hdr);
+             scan_ticket, &hdr->n_vis, hdr);
   // 2. depth sort: 31 bits (z > 0, so the sign bit is clear)
   cudaError_t err = radix_sort(vk0, vv0, vk1, vv1, &hdr->n_vis, L.E, L.nb_E, 32, at<void>(ws, L.sortaux[0]),
                                L.sortaux_bytes[0], hdr, s);
@@ -750,17 +752,15 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   uint32_t* pair_off = at<uint32_t>(ws, L.pair_off);
   uint32_t* chunk_first = at<uint32_t>(ws, L.chunk_first);
   const int64_t n_chunks = (L.Pcap + kEmitChunk - 1) / kEmitChunk + 1;
-  launch_pdl(k_pair_offsets, L.nb_E, kSortThreads, 0, s, vv0, &hdr->n_vis, L.E, touched, pair_off, chunk_first, n_chunks,
-                                                  scan_words + L.nb_E, scan_ticket + 1, &hdr->n_pairs, L.Pcap,
-                                                  hdr);
+  launch_pdl(k_pair_offsets, L.nb_E, kSortThreads, 0, s, vv0, &hdr->n_vis, L.E, touched, pair_off, chunk_first,
+             n_chunks, scan_words + L.nb_E, scan_ticket + 1, &hdr->n_pairs, L.Pcap, hdr);
   // 4. emission
   // (the emission also counts the tile keys' digits for the sort)
   const int bits = tile_sort_bits(L.T);
   const int tile_passes = (bits + kRadixBits - 1) / kRadixBits;
   const int eg = (int)std::min<int64_t>((L.Pcap + kEmitChunk - 1) / kEmitChunk, 148 * 8);
   launch_pdl(k_emit, eg, kSortThreads, 0, s, fd, vv0, &hdr->n_vis, &hdr->n_pairs, L.E, at<short4>(ws, L.rect),
-                                     pair_off, L.Pcap, pt0, pv0, chunk_first, n_chunks, tile_passes,
-                                     at<uint32_t>(ws, L.sortaux[1]));
+             pair_off, L.Pcap, pt0, pv0, chunk_first, n_chunks, tile_passes, at<uint32_t>(ws, L.sortaux[1]));
   // 5. tile sort
   err = radix_sort(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, at<void>(ws, L.sortaux[1]),
                    L.sortaux_bytes[1], hdr, s);

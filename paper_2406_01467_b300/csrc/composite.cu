@@ -253,10 +253,9 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
     uint32_t cm = 0;        // records of the chunk this lane blends
     // Two records per round, the odd one alone: both alphas are computed
     // before the blends (the chain through T is the only serial part).
-    // Branch-free: a lane that is
-    // done, whose alpha misses the cut, or whose transmittance would fall below
-    // T_min blends with alpha 0, which leaves every sum and T exactly as they
-    // were (w = 0 adds +/-0).
+    // Branch-free: a lane that is done, whose alpha misses the cut, or whose
+    // transmittance would fall below T_min blends with alpha 0, which leaves
+    // every sum and T exactly as they were (w = 0 adds +/-0).
     auto blend_one = [&](int j, float al0, float4 b, float2 d) {
       const float Tn = T * (1.f - al0);
       const bool hit = !done && al0 >= amin;
@@ -730,7 +729,8 @@ static cudaError_t launch_fwd_variant(const FrameDev* fd, void* ws, const Layout
         cudaFuncSetAttribute(k_render_fwd<LOSS, GEO, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  launch_pdl(k_render_fwd<LOSS, GEO, CH>, persistent_grid(k_render_fwd<LOSS, GEO, CH>, n_items, smem), kRenderThreads, smem, s, fd, ws, L, maps, subs, n_items);
+  launch_pdl(k_render_fwd<LOSS, GEO, CH>, persistent_grid(k_render_fwd<LOSS, GEO, CH>, n_items, smem),
+             kRenderThreads, smem, s, fd, ws, L, maps, subs, n_items);
   return cudaGetLastError();
 }
 
@@ -778,7 +778,7 @@ cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& hf, con
   {
     const int g = (int)std::min<int64_t>(std::max<int64_t>((4 * L.E + 255) / 256, 1), 148 * 16);
     launch_pdl(k_bwd_clear, g, 256, 0, s, at<uint32_t>(ws, L.vval[0]), &hdr->n_vis, L.E, at<float4>(ws, L.grad2d),
-                                  at<BwdCounters>(ws, L.bwdcnt));
+               at<BwdCounters>(ws, L.bwdcnt));
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
@@ -786,9 +786,11 @@ cudaError_t launch_render_bwd(void* ws, const Layout& L, const FrameDev& hf, con
   const int subs = hf.tile_w * hf.tile_h / 32;
   const int n_items = (int)L.T * subs;
   if (hf.losses && (g.ddist || g.dnloss))
-    launch_pdl(k_render_bwd<true>, persistent_grid(k_render_bwd<true>, n_items), kRenderThreads, 0, s, fd, ws, L, g, subs, n_items);
+    launch_pdl(k_render_bwd<true>, persistent_grid(k_render_bwd<true>, n_items), kRenderThreads, 0, s, fd, ws, L, g,
+               subs, n_items);
   else
-    launch_pdl(k_render_bwd<false>, persistent_grid(k_render_bwd<false>, n_items), kRenderThreads, 0, s, fd, ws, L, g, subs, n_items);
+    launch_pdl(k_render_bwd<false>, persistent_grid(k_render_bwd<false>, n_items), kRenderThreads, 0, s, fd, ws, L,
+               g, subs, n_items);
   return cudaGetLastError();
 }
 

@@ -805,7 +805,8 @@ cudaError_t launch_preprocess(void* ws, const Layout& L, const FrameDev& hf, cud
   cudaError_t e = cudaSuccess;
   if (hf.geometry_only) {   // one launch per dtype, SH not read
     if (k & (0xFu << (4 * GS_F32))) launch_pdl(k_preprocess<float, 0, true>, grid, kPreThreads, 0, s, fd, ws, L);
-    if (k & (0xFu << (4 * GS_BF16))) launch_pdl(k_preprocess<__nv_bfloat16, 0, true>, grid, kPreThreads, 0, s, fd, ws, L);
+    if (k & (0xFu << (4 * GS_BF16)))
+      launch_pdl(k_preprocess<__nv_bfloat16, 0, true>, grid, kPreThreads, 0, s, fd, ws, L);
     return cudaGetLastError();
   }
   for (int deg = 0; deg < 4 && e == cudaSuccess; ++deg) {
