@@ -56,7 +56,11 @@ typedef enum {
   GS_ERR_CAPACITY = 2,    /* more (tile, Gaussian) pairs than pair_capacity */
   GS_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
   GS_ERR_TIMEOUT = 4,     /* a bounded device wait ran out (scan / radix-sort look-back) */
-  GS_ERR_NUMERIC = 5      /* non-finite inputs; those Gaussians were culled */
+  GS_ERR_NUMERIC = 5,     /* non-finite inputs; those Gaussians were culled */
+  GS_ERR_BOUNDS = 6       /* only in a library built with -DGS_DEBUG (gs_debug_checks):
+                             an index into a workspace buffer was out of range, a
+                             library fault; the access was skipped and gs_check names
+                             the site and the index */
 } gs_status;
 
 typedef enum { GS_F32 = 0, GS_BF16 = 1 } gs_dtype;
@@ -350,6 +354,15 @@ gs_status gs_check(const gs_frame* frame, gs_stats* out, void* stream);
  * frame's workspace (its binning words, which the next gs_bin clears); the
  * frame must have been prepared as for gs_preprocess. */
 gs_status gs_debug_wait_timeout(const gs_frame* frame, int32_t spin_limit, void* stream);
+
+/* 1 if this library was built with -DGS_DEBUG, else 0.  Such a build checks
+ * the data-dependent indices of the device code (the entries named by the
+ * tile lists, the tiles named by the pairs, the radix sort's scatter
+ * destinations) before it uses them; an index out of range skips the access,
+ * is recorded in the workspace (the first one of a frame) and sets the sticky
+ * status to GS_ERR_BOUNDS.  Its results are otherwise those of the ordinary
+ * build.  A stand-in for a memory checker: a test harness, not the product. */
+int32_t gs_debug_checks(void);
 
 /* ---- Throughput probes (measurement support; the paper has no counterpart) --
  * The compositing kernels are bound by instruction issue, the FP32 and MUFU

@@ -12,12 +12,13 @@ from ctypes import POINTER, Structure, c_float, c_int32, c_int64, c_size_t, c_vo
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgs.so")
+DEBUG_LIB_PATH = os.path.join(HERE, "libgs_debug.so")   # -DGS_DEBUG: device bounds checks (tests only)
 
-GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_NUMERIC = range(6)
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_NUMERIC, GS_ERR_BOUNDS = range(7)
 GS_F32, GS_BF16 = 0, 1
 GS_MAX_VIEWS, GS_MAX_SCENES = 64, 16
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_CUDA",
-                4: "GS_ERR_TIMEOUT", 5: "GS_ERR_NUMERIC"}
+                4: "GS_ERR_TIMEOUT", 5: "GS_ERR_NUMERIC", 6: "GS_ERR_BOUNDS"}
 
 
 class GsScene(Structure):
@@ -78,11 +79,11 @@ class GsStats(Structure):
 EXPORTS = ("gs_workspace_size", "gs_preprocess", "gs_bin", "gs_render_fwd", "gs_render_bwd",
            "gs_composite_bwd", "gs_preprocess_bwd", "gs_filter3d", "gs_appearance_param_count",
            "gs_appearance_fwd_bwd", "gs_adam_step", "gs_debug_copy", "gs_render_fwd_static",
-           "gs_check", "gs_debug_wait_timeout", "gs_peak_probe", "gs_last_error_string")
+           "gs_check", "gs_debug_wait_timeout", "gs_peak_probe", "gs_debug_checks", "gs_last_error_string")
 GS_PEAK_FFMA, GS_PEAK_FFMA2, GS_PEAK_EX2, GS_PEAK_LDS128 = range(4)
 STATIC_SCRATCH_BYTES = 32 << 20
 
-_lib = None
+_libs = {}   # path -> loaded library
 
 
 class GsError(RuntimeError):
@@ -92,13 +93,14 @@ class GsError(RuntimeError):
 
 
 def load(path: str = LIB_PATH):
-    """Load libgs.so and declare its prototypes (raises if it is missing)."""
-    global _lib
-    if _lib is not None:
-        return _lib
+    """Load libgs.so (or another build of it, e.g. DEBUG_LIB_PATH) and declare
+    its prototypes; raises if it is missing."""
+    if path in _libs:
+        return _libs[path]
     if not os.path.exists(path):
-        raise ImportError(f"libgs.so not found at {path}: build it with "
-                          f"`python -m paper_2406_01467_b300.build`")
+        raise ImportError(f"{os.path.basename(path)} not found at {path}: build it with "
+                          f"`python -m paper_2406_01467_b300.build`"
+                          f"{' --debug' if path == DEBUG_LIB_PATH else ''}")
     lib = ctypes.CDLL(path)
     pf = POINTER(GsFrame)
     lib.gs_workspace_size.argtypes = [pf]
@@ -137,11 +139,15 @@ def load(path: str = LIB_PATH):
     lib.gs_peak_probe.restype = c_int32
     lib.gs_last_error_string.argtypes = []
     lib.gs_last_error_string.restype = ctypes.c_char_p
-    _lib = lib
+    lib.gs_debug_checks.argtypes = []
+    lib.gs_debug_checks.restype = c_int32
+    _libs[path] = lib
     return lib
 
 
-def check(status: int, what: str = ""):
+def check(status: int, what: str = "", lib=None):
+    """Raise GsError for a non-OK status, with the message of the library that
+    returned it (`lib`, default libgs.so)."""
     if status != GS_OK:
-        msg = load().gs_last_error_string().decode()
+        msg = (lib or load()).gs_last_error_string().decode()
         raise GsError(status, f"{what}: {msg}" if what else msg)

@@ -324,7 +324,7 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
        const unsigned long long* n_vis_ptr, const unsigned long long* n_pairs_ptr, int64_t E,
        const short4* __restrict__ rect, const uint32_t* __restrict__ pair_off, int64_t cap,
        uint32_t* __restrict__ ptile, uint32_t* __restrict__ pval, const uint32_t* __restrict__ chunk_first,
-       int64_t n_chunks, int tile_passes, uint32_t* __restrict__ ghist) {
+       int64_t n_chunks, int tile_passes, uint32_t* __restrict__ ghist, int64_t T, Header* hdr) {
   pdl_wait();
   pdl_trigger();
   // per entry of the slice: its first pair, and (entry, first tile of its
@@ -415,6 +415,8 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
         int tx = local - ty * nx;
         if (tx < 0) { --ty; tx += nx; } else if (tx >= nx) { ++ty; tx -= nx; }
         t = en.y + (uint32_t)(ty * rowlen + tx);
+        (void)GS_IN_BOUNDS(hdr, t < T, BS_EMIT_TILE, t);
+        (void)GS_IN_BOUNDS(hdr, en.x < E, BS_EMIT_ENTRY, en.x);
         ptile[p0 + i] = t;
         pval[p0 + i] = en.x;
       }
@@ -429,7 +431,7 @@ k_emit(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ sval,
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_ranges(const uint32_t* __restrict__ ptile, const unsigned long long* n_pairs_ptr, int64_t cap,
-         int2* __restrict__ ranges) {
+         int2* __restrict__ ranges, int64_t T, Header* hdr) {
   pdl_wait();
   pdl_trigger();
   const int64_t P = clamp_count(n_pairs_ptr, cap);
@@ -451,6 +453,7 @@ k_ranges(const uint32_t* __restrict__ ptile, const unsigned long long* n_pairs_p
     for (int k = 0; k < 4; ++k) {
       const int64_t i = i0 + k;
       if (i >= P) break;
+      if (!GS_IN_BOUNDS(hdr, t[k + 1] < T, BS_RANGE_TILE, t[k + 1])) continue;
       if (i == 0 || t[k] != t[k + 1]) ranges[t[k + 1]].x = (int)i;
       if (i == P - 1 || t[k + 2] != t[k + 1]) ranges[t[k + 1]].y = (int)(i + 1);
     }
@@ -685,8 +688,10 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
     const uint32_t kk = s_keys[i];
     const int dd = (int)((kk >> shift) & (kRadix - 1));
     const uint32_t dst = s_gbase[dd] + (uint32_t)i - s_dstart[dd];
-    kout[dst] = kk;
-    vout[dst] = s_vals[i];
+    if (GS_IN_BOUNDS(hdr, dst < n, BS_SORT_DST, dst)) {
+      kout[dst] = kk;
+      vout[dst] = s_vals[i];
+    }
   }
 }
 
@@ -760,7 +765,8 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   const int tile_passes = (bits + kRadixBits - 1) / kRadixBits;
   const int eg = (int)std::min<int64_t>((L.Pcap + kEmitChunk - 1) / kEmitChunk, 148 * 8);
   launch_pdl(k_emit, eg, kSortThreads, 0, s, fd, vv0, &hdr->n_vis, &hdr->n_pairs, L.E, at<short4>(ws, L.rect),
-             pair_off, L.Pcap, pt0, pv0, chunk_first, n_chunks, tile_passes, at<uint32_t>(ws, L.sortaux[1]));
+             pair_off, L.Pcap, pt0, pv0, chunk_first, n_chunks, tile_passes, at<uint32_t>(ws, L.sortaux[1]), L.T,
+             hdr);
   // 5. tile sort
   err = radix_sort(pt0, pv0, pt1, pv1, &hdr->n_pairs, L.Pcap, L.nb_P, bits, at<void>(ws, L.sortaux[1]),
                    L.sortaux_bytes[1], hdr, s);
@@ -768,7 +774,7 @@ cudaError_t launch_bin(void* ws, const Layout& L, const FrameDev& hf, cudaStream
   uint32_t* ptile = at<uint32_t>(ws, L.ptile_final);
   // 6. ranges
   int g = (int)std::max<int64_t>(1, std::min<int64_t>((L.Pcap / 4 + 255) / 256, 148 * 16));
-  launch_pdl(k_ranges, g, 256, 0, s, ptile, &hdr->n_pairs, L.Pcap, at<int2>(ws, L.ranges));
+  launch_pdl(k_ranges, g, 256, 0, s, ptile, &hdr->n_pairs, L.Pcap, at<int2>(ws, L.ranges), L.T, hdr);
   // 7. compositing work order (by list length)
   return launch_tile_order(ws, L, nullptr, at<int>(ws, L.tile_order), s);
 }

@@ -202,6 +202,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   const int2 range = at<int2>(ws, L.ranges)[tile];
   const uint32_t* pval = at<uint32_t>(ws, L.pval_final);
   const float4* rec = at<float4>(ws, L.rec);
+  Header* hdr = at<Header>(ws, L.hdr);   // (bounds checks of a GS_DEBUG build)
   const float amin = fd->alpha_min, amax = fd->alpha_max, tmin = fd->T_min, tmed = fd->median_T;
   const float lg_amin = __log2f(amin);
   const float fpx = c.px + 0.5f, fpy = c.py + 0.5f;
@@ -225,8 +226,10 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   if (range.x < range.y) {
 #pragma unroll
     for (int q = 0; q < NS; ++q)
-      if (range.x + 32 * q + lane < range.y)
-        stage_record<LOSS>(buf[0][q], lane, rec + 4 * (int64_t)__ldg(pval + range.x + 32 * q + lane));
+      if (range.x + 32 * q + lane < range.y) {
+        const uint32_t e = __ldg(pval + range.x + 32 * q + lane);
+        if (GS_IN_BOUNDS(hdr, e < L.E, BS_FWD_ENTRY, e)) stage_record<LOSS>(buf[0][q], lane, rec + 4 * (int64_t)e);
+      }
     cp_async_commit();
 #pragma unroll
     for (int q = 0; q < NS; ++q)
@@ -236,7 +239,8 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
     if (__all_sync(kFull, done)) break;
 #pragma unroll
     for (int q = 0; q < NS; ++q)
-      if (c00 + CH + 32 * q + lane < range.y) stage_record<LOSS>(buf[cur ^ 1][q], lane, rec + 4 * (int64_t)e_next[q]);
+      if (c00 + CH + 32 * q + lane < range.y && GS_IN_BOUNDS(hdr, e_next[q] < L.E, BS_FWD_ENTRY, e_next[q]))
+        stage_record<LOSS>(buf[cur ^ 1][q], lane, rec + 4 * (int64_t)e_next[q]);
     cp_async_commit();
 #pragma unroll
     for (int q = 0; q < NS; ++q)
@@ -333,7 +337,7 @@ __device__ inline void fwd_item(const FrameDev* __restrict__ fd, void* __restric
   // never reached: the last contributor's
   const bool have = LOSS && med >= 0;
   if (med < 0) med = last;
-  if (!have && med >= 0) {
+  if (!have && med >= 0 && GS_IN_BOUNDS(hdr, pval[med] < L.E, BS_FWD_ENTRY, pval[med])) {
     const float4* r = rec + 4 * (int64_t)pval[med];
     const float4 a = r[0], e2 = r[2];
     depth = e2.z + e2.x * (a.x - fpx) + e2.y * (a.y - fpy);
@@ -446,6 +450,7 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
   const uint32_t* pval = at<uint32_t>(ws, L.pval_final);
   const float4* rec = at<float4>(ws, L.rec);
   float* grad = at<float>(ws, L.grad2d);
+  Header* hdr = at<Header>(ws, L.hdr);   // (bounds checks of a GS_DEBUG build)
   const float amin = fd->alpha_min, amax = fd->alpha_max;
   const float fpx = c.px + 0.5f, fpy = c.py + 0.5f;
   const int lane = threadIdx.x & 31;
@@ -493,11 +498,13 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
     // depth sums gain dD (1, dx, dy), added here once per pixel instead of in
     // every visit's reduction
     const uint32_t e = pval[med];
-    const float4 a = rec[4 * (int64_t)e];
-    float* row = grad + (int64_t)e * kRecFloats;
-    atomicAdd(row + G_Z, dD);
-    atomicAdd(row + G_P0, dD * (a.x - fpx));
-    atomicAdd(row + G_P1, dD * (a.y - fpy));
+    if (GS_IN_BOUNDS(hdr, e < L.E, BS_BWD_ENTRY, e)) {
+      const float4 a = rec[4 * (int64_t)e];
+      float* row = grad + (int64_t)e * kRecFloats;
+      atomicAdd(row + G_Z, dD);
+      atomicAdd(row + G_P0, dD * (a.x - fpx));
+      atomicAdd(row + G_P1, dD * (a.y - fpy));
+    }
   }
 
   float T = Tf;
@@ -531,7 +538,8 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
     if (wm == 0) continue;
     const int c0 = range.x + 32 * k;
     if ((wm >> lane) & 1u) {   // copies straight to shared memory, no registers
-      stage_record<LOSS, false>(my, lane, rec + 4 * (int64_t)e_cur);
+      if (GS_IN_BOUNDS(hdr, e_cur < L.E, BS_BWD_ENTRY, e_cur))
+        stage_record<LOSS, false>(my, lane, rec + 4 * (int64_t)e_cur);
       my_e[lane] = e_cur;
     }
     cp_async_commit();
@@ -630,7 +638,8 @@ __device__ inline void bwd_item(const FrameDev* __restrict__ fd, void* __restric
       const float s = reduce_rows<NP>(my_red);   // lanes 16-31 read stale rows without jB
       __syncwarp();   // the scratch is rewritten by the next round
       const int j = lane < 16 ? jA : jB;
-      if (j >= 0 && slot != G_UNUSED && s != 0.f) atomicAdd(grad + (int64_t)my_e[j] * kRecFloats + slot, s);
+      if (j >= 0 && slot != G_UNUSED && s != 0.f && GS_IN_BOUNDS(hdr, my_e[j] < L.E, BS_BWD_ENTRY, my_e[j]))
+        atomicAdd(grad + (int64_t)my_e[j] * kRecFloats + slot, s);
     }
     __syncwarp();
   }

@@ -129,7 +129,8 @@ struct Header {
   int32_t pad0_;
   int32_t status;
   uint32_t filter_max;          // bits of the largest 3D-filter variance of seen Gaussians
-  int32_t pad_[50];
+  unsigned long long debug_word;   // GS_DEBUG builds: the frame's first index out of range
+  int32_t pad_[48];
 };
 
 // Counters of the compositing backward; they sit right before the 2D-gradient
@@ -196,6 +197,33 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 __device__ inline void set_status(Header* h, int code) {
   atomicCAS(&h->status, 0, code);
 }
+
+// Bounds checks of a GS_DEBUG build.  GS_IN_BOUNDS(h, ok, site, index) is
+// `ok`, and when `ok` is false it records (site, index) as the frame's first
+// violation (bit 63 set, the site in bits 48-62, the index in bits 0-47) and
+// sets the status to GS_ERR_BOUNDS; the caller skips the access.  In an
+// ordinary build it is the constant true, and the code is that of no check.
+enum BoundsSite : int {
+  BS_FWD_ENTRY = 1,   // compositing forward: a tile list's entry
+  BS_BWD_ENTRY = 2,   // compositing backward: a tile list's entry
+  BS_RANGE_TILE = 3,  // tile ranges: a pair's tile
+  BS_SORT_DST = 4,    // radix sort: a scatter destination
+  BS_EMIT_TILE = 5,   // emission: a pair's tile
+  BS_EMIT_ENTRY = 6,  // emission: a pair's entry
+};
+#ifdef GS_DEBUG
+__device__ inline bool gs_in_bounds(Header* h, bool ok, int site, int64_t index) {
+  if (!ok) {
+    const unsigned long long w =
+        (1ull << 63) | ((unsigned long long)site << 48) | ((unsigned long long)index & 0xFFFFFFFFFFFFull);
+    if (atomicCAS(&h->debug_word, 0ull, w) == 0ull) set_status(h, GS_ERR_BOUNDS);
+  }
+  return ok;
+}
+#define GS_IN_BOUNDS(h, ok, site, index) gs_in_bounds((h), (ok), (site), (int64_t)(index))
+#else
+#define GS_IN_BOUNDS(h, ok, site, index) true
+#endif
 
 __device__ inline int find_view(const int64_t* off, int n_views, int64_t e) {
   int lo = 0, hi = n_views - 1;

@@ -117,8 +117,9 @@ class Frame:
     (one host synchronisation) and the workspace is grown when needed."""
 
     def __init__(self, scenes: Sequence[SceneTensors], views, params: RenderParams = None,
-                 pair_capacity: Optional[int] = None):
-        self.lib = _lib.load()
+                 pair_capacity: Optional[int] = None, lib=None):
+        # `lib`: another build of the library (e.g. _lib.load(_lib.DEBUG_LIB_PATH))
+        self.lib = lib if lib is not None else _lib.load()
         self.scenes = list(scenes)
         self.views = list(views)
         self.params = params or RenderParams()
@@ -152,6 +153,9 @@ class Frame:
         self._maps = GsMaps(_ptr(self.color), _ptr(self.alpha), _ptr(self.depth), _ptr(self.normal),
                             _ptr(self.dist), _ptr(self.nloss))
 
+    def _check(self, status, what):
+        check(status, what, self.lib)
+
     def _bind_scenes(self):
         for i, s in enumerate(self.scenes):
             self._c_scenes[i] = GsScene(_ptr(s.means), _ptr(s.scales), _ptr(s.quats), _ptr(s.opacities),
@@ -172,7 +176,7 @@ class Frame:
         self.frame.workspace_bytes = 0
         size = self.lib.gs_workspace_size(ctypes.byref(self.frame))
         if size == 0:
-            check(_lib.GS_ERR_INVALID_ARG, "gs_workspace_size")
+            self._check(_lib.GS_ERR_INVALID_ARG, "gs_workspace_size")
         self.ws = torch.empty(size + 256, dtype=torch.uint8, device=self.device)
         base = self.ws.data_ptr()
         aligned = (base + 255) // 256 * 256
@@ -182,13 +186,13 @@ class Frame:
 
     # ------------------------------------------------------------------
     def preprocess(self, stream=None):
-        check(self.lib.gs_preprocess(ctypes.byref(self.frame), _stream(stream)), "gs_preprocess")
+        self._check(self.lib.gs_preprocess(ctypes.byref(self.frame), _stream(stream)), "gs_preprocess")
 
     def bin(self, stream=None):
-        check(self.lib.gs_bin(ctypes.byref(self.frame), _stream(stream)), "gs_bin")
+        self._check(self.lib.gs_bin(ctypes.byref(self.frame), _stream(stream)), "gs_bin")
 
     def render(self, stream=None):
-        check(self.lib.gs_render_fwd(ctypes.byref(self.frame), ctypes.byref(self._maps),
+        self._check(self.lib.gs_render_fwd(ctypes.byref(self.frame), ctypes.byref(self._maps),
                                      _stream(stream)), "gs_render_fwd")
 
     def stats(self, stream=None) -> GsStats:
@@ -207,7 +211,7 @@ class Frame:
                 self.bin(stream)
                 st = self.stats(stream)
             if self.last_status not in (GS_OK, _lib.GS_ERR_NUMERIC):
-                check(self.last_status, "binning")
+                self._check(self.last_status, "binning")
         self.render(stream)
 
     def filter3d(self, scene: int = 0, scale: float = 0.2, attach: bool = True, stream=None):
@@ -215,7 +219,7 @@ class Frame:
         (FP32 (N,)); with ``attach`` the scene renders with them from now on."""
         s = self.scenes[scene]
         out = torch.empty(s.n, dtype=torch.float32, device=self.device)
-        check(self.lib.gs_filter3d(ctypes.byref(self.frame), int(scene), float(scale), _ptr(out),
+        self._check(self.lib.gs_filter3d(ctypes.byref(self.frame), int(scene), float(scale), _ptr(out),
                                    _stream(stream)), "gs_filter3d")
         if attach:
             s.filter_var = out
@@ -258,16 +262,16 @@ class Frame:
                                  _ptr(g["opacities"]), _ptr(g["sh"]))
         self._cg, self._mg = cg, mg
         if not split:
-            check(self.lib.gs_render_bwd(ctypes.byref(self.frame), ctypes.byref(mg), cg, _stream(stream)),
+            self._check(self.lib.gs_render_bwd(ctypes.byref(self.frame), ctypes.byref(mg), cg, _stream(stream)),
                   "gs_render_bwd")
             return grads
         if events:
             events[0].record()
-        check(self.lib.gs_composite_bwd(ctypes.byref(self.frame), ctypes.byref(mg), _stream(stream)),
+        self._check(self.lib.gs_composite_bwd(ctypes.byref(self.frame), ctypes.byref(mg), _stream(stream)),
               "gs_composite_bwd")
         if events:
             events[1].record()
-        check(self.lib.gs_preprocess_bwd(ctypes.byref(self.frame), cg, _stream(stream)),
+        self._check(self.lib.gs_preprocess_bwd(ctypes.byref(self.frame), cg, _stream(stream)),
               "gs_preprocess_bwd")
         if events:
             events[2].record()
@@ -295,7 +299,7 @@ class Frame:
     def debug_wait_timeout(self, spin_limit: int = 1000, stream=None):
         """Runs the device's bounded-wait test hook (a poll that nothing answers);
         the frame's status then reads GS_ERR_TIMEOUT until the next preprocess."""
-        check(self.lib.gs_debug_wait_timeout(ctypes.byref(self.frame), int(spin_limit), _stream(stream)),
+        self._check(self.lib.gs_debug_wait_timeout(ctypes.byref(self.frame), int(spin_limit), _stream(stream)),
               "gs_debug_wait_timeout")
 
     def debug(self):
@@ -310,7 +314,7 @@ class Frame:
         pe = torch.zeros(P, dtype=torch.int32, device=dev)
         rg = torch.zeros((T, 2), dtype=torch.int32, device=dev)
         g2 = None if self.params.geometry_only else torch.zeros((E, 16), dtype=torch.float32, device=dev)
-        check(self.lib.gs_debug_copy(ctypes.byref(self.frame), _ptr(rec), _ptr(rect), _ptr(pt), _ptr(pe),
+        self._check(self.lib.gs_debug_copy(ctypes.byref(self.frame), _ptr(rec), _ptr(rect), _ptr(pt), _ptr(pe),
                                      _ptr(rg), _ptr(g2), _stream(None)), "gs_debug_copy")
         st = self.stats()
         n = int(min(st.n_pairs, P))

@@ -155,3 +155,12 @@ def test_appearance_param_count_and_validation(lib):
     st = lib.gs_appearance_fwd_bwd(ctypes.byref(f), ctypes.byref(app), idx, 256, 256, None, None, None, 256, None)
     assert st == _lib.GS_ERR_INVALID_ARG and "embedding index" in lib.gs_last_error_string().decode()
     assert lib.gs_adam_step(256, 256, 256, 256, 10, 0.01, 0.9, 0.999, 1e-8, 0, 1, None) == _lib.GS_ERR_INVALID_ARG
+
+
+def test_debug_build_reports_its_checks_and_exports_the_same_symbols(lib):
+    assert lib.gs_debug_checks() == 0
+    build.build(debug=True)
+    dbg = _lib.load(_lib.DEBUG_LIB_PATH)
+    assert dbg is not lib and dbg.gs_debug_checks() == 1
+    for n in _declared_functions():
+        assert hasattr(dbg, n), n
