@@ -79,3 +79,57 @@ def test_geometry_only(libs):
 
 def test_capacity_overflow_then_grown(libs):
     _compare(libs, [scenes.tiny_scene()], [(scenes.tiny_camera(), 0)], RenderParams(), cap=100)
+
+
+def _corrupt_pair_entries(fr, tile, value=-1):
+    """Overwrite the entries of one tile's list in the frame's workspace (found
+    by matching the sorted pair entries that gs_debug_copy returns)."""
+    d = fr.debug()
+    pe, rg = d["pair_entry"], d["ranges"]
+    base = (fr.ws.data_ptr() + 255) // 256 * 256 - fr.ws.data_ptr()
+    words = fr.ws[base:base + (fr.ws.numel() - base) // 4 * 4].view(torch.int32)
+    n = pe.numel()
+    cand = torch.nonzero(words[: words.numel() - n + 1] == pe[0]).flatten().tolist()
+    hits = [c for c in cand if torch.equal(words[c:c + n], pe)]
+    assert len(hits) == 1, hits
+    lo, hi = int(rg[tile, 0]), int(rg[tile, 1])
+    assert hi > lo
+    words[hits[0] + lo:hits[0] + hi] = value
+    return lo, hi
+
+
+def _largest_tile(fr):
+    rg = fr.debug()["ranges"]
+    return int(torch.argmax(rg[:, 1] - rg[:, 0]))
+
+
+def test_a_corrupted_tile_list_is_caught_by_the_forward(libs):
+    _, dbg = libs
+    assert dbg.gs_debug_checks() == 1   # never run a corrupted workspace through the ordinary build
+    st = SceneTensors.from_scene(scenes.tiny_scene(), DEV)
+    fr = Frame([st], [(scenes.tiny_camera(), 0)], RenderParams(), lib=dbg)
+    fr.forward()
+    assert fr.stats().status == 0
+    _corrupt_pair_entries(fr, _largest_tile(fr))
+    fr.render()
+    fr.stats()
+    assert fr.last_status == _lib.GS_ERR_BOUNDS
+    msg = dbg.gs_last_error_string().decode()
+    assert "compositing forward: tile-list entry" in msg and "4294967295" in msg, msg
+
+
+def test_a_corrupted_tile_list_is_caught_by_the_backward(libs):
+    _, dbg = libs
+    assert dbg.gs_debug_checks() == 1
+    cam = scenes.tiny_camera()
+    st = SceneTensors.from_scene(scenes.tiny_scene(), DEV)
+    fr = Frame([st], [(cam, 0)], RenderParams(), lib=dbg)
+    fr.forward()
+    assert fr.stats().status == 0
+    _corrupt_pair_entries(fr, _largest_tile(fr))
+    up = [torch.from_numpy(u[0]).to(DEV) for u in scenes.upstream_grads(3, cam.height, cam.width)]
+    fr.backward(*up)
+    fr.stats()
+    assert fr.last_status == _lib.GS_ERR_BOUNDS
+    msg = dbg.gs_last_error_string().decode()
+    assert "compositing backward: tile-list entry" in msg and "4294967295" in msg, msg
