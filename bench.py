@@ -542,6 +542,8 @@ def run_ours(args, rank, world, device):
         "counts": {"visible": nvis, "pairs": P, "blended": nbl, "evals_fwd": ev_f, "evals_bwd": ev_b},
         "clocks": clocks, "e2e": e2e, "unit_peaks": units,
         "gpu_launches": launches_per_step(frame_tiles(cam, params)) * args.steps,
+        # the timed frame's maps, for the CPU-baseline leg's oracle comparison (not printed)
+        "_maps": [m.detach().cpu().numpy() for m in frame.view_maps(0)],
     }
     return out
 
@@ -758,14 +760,15 @@ def run_batched(args, device):
 # --------------------------------------------------------------------------------------
 # CPU oracle (baseline arm and cpu_baseline field)
 # --------------------------------------------------------------------------------------
-def oracle_step(scene, cam, seed, crop=32, grid=4):
+def oracle_step(scene, cam, seed, crop=32, grid=4, collect=None):
     """One step of the CPU oracle on a bounded sample of the frame: its FP32
     binning decisions over all Gaussians, then forward + gradients for grid x
     grid crops of crop x crop pixels, one at a seeded position in each cell of
     a grid x grid partition of the image (stratified, so every step samples
     the whole frame), each restricted to the Gaussians whose rectangles reach
     it.  Returns (estimated ms for the whole frame, seconds spent, sampled
-    pixels): binning time + crop time scaled by pixels."""
+    pixels): binning time + crop time scaled by pixels.  ``collect`` (a list)
+    receives (pixels, oracle maps) of every crop."""
     import oracle
     from oracle import binning
     from paper_2406_01467_b300 import scenes
@@ -791,19 +794,54 @@ def oracle_step(scene, cam, seed, crop=32, grid=4):
             ys, xs = np.mgrid[y0:y0 + crop, x0:x0 + crop]
             pix = (ys * cam.width + xs).reshape(-1)
             t1 = time.perf_counter()
-            oracle.render_grads(sub, cam, up, p, pixels=pix)
+            _, _, maps = oracle.render_grads(sub, cam, up, p, pixels=pix)
             t_crop += time.perf_counter() - t1
+            if collect is not None:
+                collect.append((pix, maps))
             n_pix += len(pix)
     est_ms = (t_dec + t_crop / n_pix * (cam.width * cam.height)) * 1e3
     return est_ms, t_dec + t_crop, n_pix
 
 
-def oracle_baseline(scene, cam, seeds, single_thread=True):
+# The map comparison of the CPU-baseline leg (the parity tests' bar): colour,
+# alpha and normal absolute, depth relative; a pixel whose alpha_min / T_min /
+# median decisions lie within AMBIG_MARGIN (relative) of their thresholds may
+# legitimately go either way in FP32 and is left out.
+TOL_ABS, TOL_DEPTH_REL, AMBIG_MARGIN = 1e-4, 1e-4, 2e-4
+
+
+def oracle_check(collected, gpu_maps):
+    """The GPU's maps of the timed frame against the FP64 oracle's on the
+    CPU-baseline sample's crops (error maps reduced to their maxima)."""
+    c, a, d, n = gpu_maps
+    pix = np.concatenate([q for q, _ in collected])
+    ref = {k: np.concatenate([m[k] for _, m in collected]) for k in ("color", "alpha", "depth", "normal", "margin")}
+    gc, gn = c.reshape(3, -1)[:, pix].T, n.reshape(3, -1)[:, pix].T
+    ga, gd = a.reshape(-1)[pix], d.reshape(-1)[pix]
+    ok = ref["margin"] >= AMBIG_MARGIN
+    ec = np.abs(gc - ref["color"]).max(axis=1)
+    ea = np.abs(ga - ref["alpha"])
+    en = np.abs(gn - ref["normal"]).max(axis=1)
+    ed = np.where(np.abs(ref["depth"]) < 1e-6, np.abs(gd - ref["depth"]),
+                  np.abs(gd - ref["depth"]) / np.maximum(np.abs(ref["depth"]), 1e-6))
+    bad = ok & ((ec > TOL_ABS) | (ea > TOL_ABS) | (en > TOL_ABS) | (ed > TOL_DEPTH_REL))
+    mx = lambda e: float(e[ok].max(initial=0.0))
+    return {"pixels": int(len(pix)), "ambiguous_excluded": round(float((~ok).mean()), 5),
+            "max_abs_color": mx(ec), "max_abs_alpha": mx(ea), "max_abs_normal": mx(en),
+            "max_rel_depth": mx(ed), "outside_tolerance": int(bad.sum()),
+            "tolerance": {"abs": TOL_ABS, "depth_rel": TOL_DEPTH_REL, "ambiguity_margin": AMBIG_MARGIN}}
+
+
+def oracle_baseline(scene, cam, seeds, single_thread=True, gpu_maps=None):
     """The oracle timed on this host over the steps ``seeds`` (oracle_step), and
-    once more on one thread.  Both arms of the benchmark use this sample."""
+    once more on one thread.  Both arms of the benchmark use this sample.  With
+    ``gpu_maps`` (the timed frame's colour, alpha, depth, normal on the host)
+    the first step's oracle maps are also compared with them (oracle_check)."""
     import torch
     cores = torch.get_num_threads()
-    est, secs, pix = zip(*[oracle_step(scene, cam, sd) for sd in seeds])
+    collected = [] if gpu_maps is not None else None
+    est, secs, pix = zip(*[oracle_step(scene, cam, sd, collect=collected if i == 0 else None)
+                           for i, sd in enumerate(seeds)])
     out = {"value": round(float(np.mean(est)), 1), "unit": "ms", "cores": cores, "kind": "oracle",
            "steps": len(seeds), "extrapolated": True, "sampled_pixels_per_step": int(pix[0]),
            "frame_pixels": int(cam.width * cam.height), "seconds": round(float(sum(secs)), 1),
@@ -818,6 +856,8 @@ def oracle_baseline(scene, cam, seeds, single_thread=True):
         finally:
             torch.set_num_threads(cores)
         out["single_thread_value"] = round(float(e1), 1)
+    if collected:
+        out["oracle_check"] = oracle_check(collected, gpu_maps)
     return out
 
 
@@ -870,6 +910,7 @@ def main():
         torch.cuda.set_device(local)
         tdist.init_process_group("nccl")
     out = run_ours(args, rank, world, f"cuda:{local}")
+    gpu_maps = out.pop("_maps", None)
     if not args.no_extras and args.config == "unbounded":
         out["bf16_graph"] = run_bf16(args, f"cuda:{local}")
         out["batched_bf16"] = run_batched_bf16(args, f"cuda:{local}", out["ms_per_step"])
@@ -880,7 +921,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the reference arm's first four steps, plus one on a single thread
         scene, cam = make_workload(args.config)
-        out["cpu_baseline"] = oracle_baseline(scene, cam, [0, 1, 2, 3])
+        out["cpu_baseline"] = oracle_baseline(scene, cam, [0, 1, 2, 3], gpu_maps=gpu_maps)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
