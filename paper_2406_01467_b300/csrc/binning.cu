@@ -532,11 +532,13 @@ cudaError_t launch_tile_order(void* ws, const Layout& L, const uint32_t* cost, i
 // often shared by a whole warp) runs three blocks per SM with `match.any`.
 // The look-back reads 4 predecessors' words per poll.
 // ---------------------------------------------------------------------------
-constexpr int kLookWindow = 4;
+constexpr int kLookWindow = 4;          // predecessors' words per poll (registers bound it)
+constexpr int kLookWindowBallot = 4;    // the same in the ballot passes, whose keys are placed first
 
 // Exclusive prefix of digit d over the blocks before blk: the predecessors'
 // words are read kLookWindow at a time, nearest first, and added up to the
 // nearest P; a window with an unpublished word before that P is read again.
+template <int kLookWindow>
 __device__ inline uint32_t digit_lookback(const unsigned long long* look, int blk, int d, Header* hdr) {
   uint32_t excl = 0;
   int j = blk - 1, spins = 0;
@@ -667,23 +669,34 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, u
   s_dstart[d] = start;
   uint32_t run = start;
   for (int i = 0; i < 8; ++i) { s_wc[0][i][d] = (uint16_t)run; run += c[i]; }   // bases <= 4096
+  // the keys in block order of digits: with ballots (two blocks per SM) before
+  // the look-back, so that their registers are free for its window
+  auto place = [&]() {
+    for (int r = 0; r < kSortItems; ++r) {
+      if (li0 + 32 * r < nloc) {
+        const int dd = (int)((k[r] >> shift) & (kRadix - 1));
+        const uint32_t pos = s_wc[0][w][dd] + rank[r];
+        s_keys[pos] = k[r];
+        s_vals[pos] = v[r];
+      }
+    }
+  };
+  if (kBallot) {
+    __syncthreads();
+    place();
+  }
   // decoupled look-back: keys of digit d in the blocks before this one
   uint32_t excl = 0;
   if (blk > 0 && gcnt) {
-    excl = digit_lookback(look, blk, d, hdr);
+    excl = digit_lookback<kBallot ? kLookWindowBallot : kLookWindow>(look, blk, d, hdr);
     st_relaxed(mine, kFlagP | (excl + cnt));
   }
   s_gbase[d] = dbase + excl;
   __syncthreads();
-  for (int r = 0; r < kSortItems; ++r) {
-    if (li0 + 32 * r < nloc) {
-      const int dd = (int)((k[r] >> shift) & (kRadix - 1));
-      const uint32_t pos = s_wc[0][w][dd] + rank[r];
-      s_keys[pos] = k[r];
-      s_vals[pos] = v[r];
-    }
+  if (!kBallot) {
+    place();
+    __syncthreads();
   }
-  __syncthreads();
   for (int i = threadIdx.x; i < nloc; i += kSortThreads) {
     const uint32_t kk = s_keys[i];
     const int dd = (int)((kk >> shift) & (kRadix - 1));
