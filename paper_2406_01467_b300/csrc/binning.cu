@@ -260,7 +260,7 @@ k_pair_offsets(const uint32_t* __restrict__ sval, const unsigned long long* n_vi
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t i = WarpItems::index(base, r);
-    cnt[r] = i < n ? __ldg(touched + __ldg(sval + i)) : 0u;
+    cnt[r] = i < n ? __ldg(touched + __ldg(sval + i)) & kTouchedMask : 0u;
   }
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {

@@ -19,6 +19,13 @@ constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 items per block
 constexpr int kRadixBits = 8;
 constexpr int kEmitChunk = 2048;          // pairs per emission slice
 constexpr int kRadix = 1 << kRadixBits;
+// Per-entry word written by the preprocess: the number of tiles the entry's
+// pixel rectangle touches (0: culled) in the low 29 bits (a view of at most
+// 32767 x 32767 pixels has fewer tiles), and in bit 29 + k whether colour
+// channel k was above 0 (not clamped by max(SH + 1/2, 0)), which the
+// preprocess backward needs.
+constexpr int kTouchedBits = 29;
+constexpr uint32_t kTouchedMask = (1u << kTouchedBits) - 1u;
 
 // The record of a (view, Gaussian) entry: four float4s
 //   #0 (u, v, a', b')             #1 (c', opacity, n_y, n_z)

@@ -437,7 +437,9 @@ k_preprocess(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout L) {
       r[3] = make_float4(rgb[0], rgb[1], rgb[2], nn[0]);
       rect[e] = make_short4((short)i0, (short)i1, (short)j0, (short)j1);
       key[e] = __float_as_uint(z);
-      touched[e] = (uint32_t)(((i1 >> sx) - (i0 >> sx) + 1) * ((j1 >> sy) - (j0 >> sy) + 1));
+      touched[e] = (uint32_t)(((i1 >> sx) - (i0 >> sx) + 1) * ((j1 >> sy) - (j0 >> sy) + 1)) |
+                   (uint32_t)(rgb[0] > 0.f) << kTouchedBits | (uint32_t)(rgb[1] > 0.f) << (kTouchedBits + 1) |
+                   (uint32_t)(rgb[2] > 0.f) << (kTouchedBits + 2);
     } else {
       rect[e] = make_short4(0, -1, 0, -1);
       key[e] = kInvalidKey;
@@ -461,9 +463,8 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
   pdl_wait();
   pdl_trigger();
   constexpr int K = (D + 1) * (D + 1);
-  const uint32_t* key = at<uint32_t>(ws, L.key);
+  const uint32_t* touched = at<uint32_t>(ws, L.touched);
   const float4* g2d = at<float4>(ws, L.grad2d);
-  const float4* rec4 = at<float4>(ws, L.rec);
   const float lp = fd->lowpass;
   // Single-view scenes store their gradients through shared memory: each thread
   // writes its rows there, then the block writes the chunk's contiguous
@@ -491,7 +492,8 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
     };
     const int64_t e = ch.e0 + (act ? t : 0), g = ch.g0 + (act ? t : 0);
     float gm[3] = {0.f, 0.f, 0.f}, gsc[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, go = 0.f;
-    if (!act || key[e] == kInvalidKey) {
+    const uint32_t tw = act ? touched[e] : 0u;   // 0: culled; else tiles and the colour clamps
+    if ((tw & kTouchedMask) == 0u) {
       if (stage_sh) {
 #pragma unroll
         for (int f = 0; f < R4; ++f) s_sh[t * R4P + f] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -506,12 +508,13 @@ k_preprocess_bwd(const FrameDev* __restrict__ fd, void* __restrict__ ws, Layout 
       const float fv = FILT ? __ldg(S.filter_var + g) : 0.f;
       if (FILT) filter3d_apply(fv, s, o);   // s, o: filtered scales and opacity
       // ---- colour first (its registers are free again before the geometry):
-      // rgb = max(sum_j Y_j c_j + 1/2, 0); a channel was clamped iff the forward
-      // record holds 0 for it
+      // rgb = max(sum_j Y_j c_j + 1/2, 0); the forward noted in the entry's
+      // touched word which channels were above 0 (the others are clamped)
       {
-        const float4 rgbf = rec4[4 * e + 3], grgb4 = g2d[4 * e + 3];
-        const float gval[3] = {rgbf.x > 0.f ? grgb4.x : 0.f, rgbf.y > 0.f ? grgb4.y : 0.f,
-                               rgbf.z > 0.f ? grgb4.z : 0.f};
+        const float4 grgb4 = g2d[4 * e + 3];
+        const float gval[3] = {(tw >> kTouchedBits) & 1u ? grgb4.x : 0.f,
+                               (tw >> (kTouchedBits + 1)) & 1u ? grgb4.y : 0.f,
+                               (tw >> (kTouchedBits + 2)) & 1u ? grgb4.z : 0.f};
         const float d[3] = {m[0] - V.campos[0], m[1] - V.campos[1], m[2] - V.campos[2]};
         const float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         const float dir[3] = {d[0] * il, d[1] * il, d[2] * il};
