@@ -57,6 +57,7 @@ def _check_all(sc, cam, p, fr, seed):
     for k in pg:
         assert np.abs(pg[k]).max() > 0, k
     assert_grads_close({k: v.cpu().numpy() for k, v in g.items()}, pg, sp, what="parameter gradients")
+    return dbg, g
 
 
 @pytest.mark.parametrize("deg", [0, 1, 2, 3])
@@ -65,6 +66,30 @@ def test_every_sh_degree_matches_oracle(deg):
     cam = _small_camera()
     p = RenderParams()
     _check_all(sc, cam, p, _frame(sc, cam, p), seed=30 + deg)
+
+
+@pytest.mark.parametrize("deg", [0, 3])
+def test_clamped_colour_channels_match_oracle(deg):
+    """A third of the splats have their red channel below 0 before the clamp
+    rgb = max(SH + 1/2, 0): the forward records red 0 for them, no gradient
+    reaches their red SH coefficients where the clamp holds, and every map and
+    gradient matches the oracle (which differentiates through the clamp)."""
+    sc = _with_degree(scenes.tiny_scene(900, seed=12), deg, seed=40 + deg)
+    sh = sc.sh.copy()
+    third = np.arange(sc.n) % 3 == 0
+    sh[third, 0, 0] = (-0.3 - 0.5) / scenes.Y00   # red -0.3 before the clamp (degree 0)
+    sc = scenes.Scene(sc.means, sc.scales, sc.quats, sc.opacities, sh, deg)
+    cam = _small_camera()
+    p = RenderParams()
+    dbg, g = _check_all(sc, cam, p, _frame(sc, cam, p), seed=50 + deg)
+    rec = dbg["rec"].cpu().numpy()
+    vis = np.zeros(sc.n, bool)
+    vis[np.unique(dbg["pair_entry"].cpu().numpy())] = True
+    red_clamped = vis & (rec[:, 12] == 0.0)
+    assert red_clamped.sum() >= 20, red_clamped.sum()   # the clamp engages on visible splats
+    if deg == 0:   # no higher band can lift red above 0: exactly the chosen third
+        assert np.array_equal(red_clamped, vis & third)
+        assert np.all(g["sh"].cpu().numpy()[vis & third, 0, 0] == 0.0)
 
 
 @pytest.mark.parametrize("deg", [1, 2])
