@@ -363,8 +363,8 @@ def rasterize(means, scales, quats, opacities, sh, camera, sh_degree: int,
     ``sync`` (default: True unless ``pair_capacity`` is given) checks the pair
     count on the host after binning and grows the workspace if needed.  With
     False nothing synchronises, so the call can be captured in a CUDA graph; a
-    frame whose pairs exceed the capacity then leaves its maps and gradients
-    unwritten and reports GS_ERR_CAPACITY through ``frame.stats()``."""
+    frame whose pairs exceed the capacity then leaves its maps unwritten, gives
+    zero gradients and reports GS_ERR_CAPACITY through ``frame.stats()``."""
     st = SceneTensors(means.detach().contiguous(), scales.detach().contiguous(),
                       quats.detach().contiguous(), opacities.detach().contiguous(),
                       sh.detach().contiguous(), sh_degree)

@@ -197,3 +197,35 @@ def test_rasterize_bf16_parameters_give_bf16_gradients():
         torch.testing.assert_close(a, b, rtol=0, atol=0)
     for a, b in zip(gb, gf):   # FP32 gradients rounded once to BF16
         torch.testing.assert_close(a.float(), b.to(torch.bfloat16).float(), rtol=1e-2, atol=1e-5 * b.abs().max().item())
+
+
+def test_rasterize_without_sync_reports_a_capacity_overflow():
+    """With a preset pair capacity below the frame's need, nothing synchronises:
+    the compositing kernels skip the frame (its maps are left unwritten and
+    its 2D gradients stay zero, so the parameter gradients come out zero), the
+    frame reports GS_ERR_CAPACITY and the pairs it needed, and a frame of that
+    size then renders and differentiates like the synchronising call."""
+    from paper_2406_01467_b300 import _lib
+    sc, cam = scenes.tiny_scene(), scenes.tiny_camera()
+    p = RenderParams()
+    up = [torch.from_numpy(u[0]).to(DEV) for u in scenes.upstream_grads(8, cam.height, cam.width)]
+    leaves = _leaves(sc)
+    small = Frame([SceneTensors.from_scene(sc, DEV)], [(cam, 0)], p, pair_capacity=64)
+    outs = rasterize(*leaves, cam, sc.sh_degree, p, pair_capacity=64, frame=small)
+    grads = torch.autograd.grad(_loss(outs, up), leaves)
+    torch.cuda.synchronize()
+    st = small.stats()
+    assert small.last_status == _lib.GS_ERR_CAPACITY and st.n_pairs > 64
+    assert all(bool((g == 0).all()) for g in grads)
+    need = int(st.n_pairs)
+    big = Frame([SceneTensors.from_scene(sc, DEV)], [(cam, 0)], p, pair_capacity=need)
+    outs_b = rasterize(*leaves, cam, sc.sh_degree, p, pair_capacity=need, frame=big)
+    grads_b = torch.autograd.grad(_loss(outs_b, up), leaves)
+    torch.cuda.synchronize()
+    assert big.stats().status == 0
+    outs_s = rasterize(*leaves, cam, sc.sh_degree, p)   # synchronising, grown as needed
+    grads_s = torch.autograd.grad(_loss(outs_s, up), leaves)
+    for a, b in zip(outs_b, outs_s):
+        torch.testing.assert_close(a, b, rtol=0, atol=0)   # the forward is deterministic
+    for a, b in zip(grads_b, grads_s):   # the backward's atomics add in any order
+        torch.testing.assert_close(a, b, rtol=1e-4, atol=1e-6 * float(b.abs().max()))
